@@ -1,0 +1,425 @@
+"""Pins for the CPU oracle: checks against facts fixed by the paper and by
+mathematics, independent of the oracle's own code.
+
+Each ``pin_*`` function raises AssertionError when the oracle (optionally a
+variant library at ``lib_path``) disagrees with the fact it pins. They are run by
+``test_oracle_pins.py`` on the real oracle and by ``test_oracle_mutations.py`` on
+copies of the oracle with planted mistakes, which each must break at least one pin.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from paper_1311_7194_b300 import synth
+
+
+# ----------------------------------------------------------------------------
+# fixtures built from plain geometry
+# ----------------------------------------------------------------------------
+
+def _plane_volume(s=2e-3, G=64, z_centre=0.5, Q=0.0, sigma=0.0, cap=4096):
+    return synth.VolumeParams(voxel_size=s, truncation=5 * s,
+                              origin=(-G / 2 * s, -G / 2 * s, z_centre - G / 2 * s), grid_dim=G,
+                              block_capacity=cap, depth_min=0.05, depth_max=5.0,
+                              raycast_near=0.05, raycast_far=5.0, sigma_coeff=sigma,
+                              process_variance=Q)
+
+
+def _voxel_world(vol, coords):
+    """World positions of voxel indices (n, 3) (voxel i sits at origin + i s)."""
+    s = float(np.float32(vol.voxel_size))
+    return np.asarray(vol.origin)[None, :] + coords.astype(np.float64) * s
+
+
+def _fuse(ov, depths, poses, vars_=None):
+    for k in range(len(depths)):
+        ov.fuse(depths[k], poses[k], None if vars_ is None else vars_[k])
+
+
+def _const_frames(n, seed, H=24, W=32, equal_var=False, d0=0.5, spread=2e-3):
+    rng = np.random.default_rng(seed)
+    D = (d0 + rng.uniform(-spread, spread, n)).astype(np.float32)
+    p = (np.full(n, 1e-6) if equal_var else rng.uniform(0.5e-6, 2e-6, n)).astype(np.float32)
+    depths = [np.full((H, W), D[k], np.float32) for k in range(n)]
+    vars_ = [np.full((H, W), p[k], np.float32) for k in range(n)]
+    return D.astype(np.float64), p.astype(np.float64), depths, vars_
+
+
+# ----------------------------------------------------------------------------
+# Alg. 3 and Eq. 9 closed forms
+# ----------------------------------------------------------------------------
+
+def pin_kalman_closed_form(lib_path=None):
+    """With Q = 0, Alg. 3 fed measurements T_k of variances p_k ends at the
+    inverse-variance weighted mean: T = sum(T_k/p_k)/sum(1/p_k), P = 1/sum(1/p_k)
+    (induction on the update). A static camera sees a fronto-parallel plane at a
+    different depth D_k each frame, so every voxel's T_k = D_k - z exactly."""
+    vol = _plane_volume()
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    n = 9
+    D, p, depths, vars_ = _const_frames(n, seed=11)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    _fuse(ov, depths, [np.eye(4)] * n, vars_)
+    e = ov.export()
+    xyz = _voxel_world(vol, oracle.voxel_coords(e))
+    Tk = D[None, :] - xyz[:, 2:3]                           # (voxels, frames)
+    delta = vol.truncation
+    all_valid = (np.abs(Tk) < delta * (1 - 1e-6)).all(1)
+    none_valid = (np.abs(Tk) > delta * (1 + 1e-6)).all(1)
+    first0 = np.repeat(e.alloc_frame == 0, 512)
+    T, P = e.T.ravel(), e.P.ravel()
+    m = all_valid & first0
+    assert m.sum() > 5000, m.sum()
+    w = 1.0 / p
+    T_exp = (Tk[m] * w).sum(1) / w.sum()
+    P_exp = 1.0 / w.sum()
+    assert np.allclose(T[m], T_exp, rtol=0, atol=1e-12), np.abs(T[m] - T_exp).max()
+    assert np.allclose(P[m], P_exp, rtol=1e-12, atol=0), np.abs(P[m] / P_exp - 1).max()
+    assert none_valid.sum() > 1000
+    assert np.isnan(T[none_valid]).all(), "voxels never within delta must stay chi"
+    # voxels inside the truncation band in some frames only: the weighted mean runs
+    # over exactly the frames whose |T_k| <= delta
+    valid = np.abs(Tk) < delta * (1 - 1e-6)
+    clear = ((np.abs(Tk) < delta * (1 - 1e-6)) | (np.abs(Tk) > delta * (1 + 1e-6))).all(1)
+    part = valid.any(1) & ~valid.all(1) & clear & first0
+    assert part.sum() > 1000, part.sum()
+    wv = np.where(valid[part], w[None, :], 0.0)
+    assert np.allclose(T[part], (Tk[part] * wv).sum(1) / wv.sum(1), rtol=0, atol=1e-12)
+    assert np.allclose(P[part], 1.0 / wv.sum(1), rtol=1e-12, atol=0)
+
+
+def pin_eq9_mean(lib_path=None):
+    """Eq. 9: N measurements of equal variance sigma^2 give their arithmetic mean
+    with variance sigma^2 / N."""
+    vol = _plane_volume()
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    n = 7
+    D, p, depths, vars_ = _const_frames(n, seed=12, equal_var=True)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    _fuse(ov, depths, [np.eye(4)] * n, vars_)
+    e = ov.export()
+    xyz = _voxel_world(vol, oracle.voxel_coords(e))
+    Tk = D[None, :] - xyz[:, 2:3]
+    m = (np.abs(Tk) < vol.truncation * (1 - 1e-6)).all(1) & np.repeat(e.alloc_frame == 0, 512)
+    assert m.sum() > 5000
+    assert np.allclose(e.T.ravel()[m], Tk[m].mean(1), rtol=0, atol=1e-12)
+    assert np.allclose(e.P.ravel()[m], p[0] / n, rtol=1e-12, atol=0)
+
+
+def pin_process_variance_steady_state(lib_path=None):
+    """With process variance Q > 0 and a constant measurement variance p, the
+    posterior variance of Alg. 3 converges to the fixed point of
+    P = (P+Q) p / (P+Q+p), i.e. P = (-Q + sqrt(Q^2 + 4 Q p)) / 2."""
+    Q, pv = 2e-7, 1e-6
+    vol = _plane_volume(Q=Q)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    n = 80
+    depths = [np.full((24, 32), 0.5, np.float32)] * n
+    vars_ = [np.full((24, 32), pv, np.float32)] * n
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    _fuse(ov, depths, [np.eye(4)] * n, vars_)
+    e = ov.export()
+    xyz = _voxel_world(vol, oracle.voxel_coords(e))
+    Tk = 0.5 - xyz[:, 2]
+    m = (np.abs(Tk) < vol.truncation * (1 - 1e-6)) & np.repeat(e.alloc_frame == 0, 512)
+    assert m.sum() > 5000
+    p32 = float(np.float32(pv))
+    Q32 = float(np.float32(Q))
+    P_inf = (-Q32 + math.sqrt(Q32 * Q32 + 4 * Q32 * p32)) / 2
+    assert np.allclose(e.P.ravel()[m], P_inf, rtol=1e-9, atol=0), np.abs(e.P.ravel()[m] / P_inf - 1).max()
+    assert np.allclose(e.T.ravel()[m], Tk[m], rtol=0, atol=1e-13)
+
+
+def pin_first_measurement_and_quadratic_variance(lib_path=None):
+    """One frame into an empty volume: T = T_k and P = p_k (first branch of
+    Alg. 3), with the default variance p_k = (a D^2)^2 of a sensor whose deviation
+    grows quadratically with depth (Introduction; Alg. 3 text); voxels with
+    |T_k| > delta hold chi (Eq. 1)."""
+    a = 1.5e-3
+    vol = _plane_volume(sigma=a)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    D = np.float32(0.5031)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    ov.fuse(np.full((24, 32), D, np.float32), np.eye(4), None)
+    e = ov.export()
+    z = _voxel_world(vol, oracle.voxel_coords(e))[:, 2]
+    Tk = float(D) - z
+    T, P = e.T.ravel(), e.P.ravel()
+    valid = np.abs(Tk) < vol.truncation * (1 - 1e-6)
+    invalid = np.abs(Tk) > vol.truncation * (1 + 1e-6)
+    assert np.allclose(T[valid], Tk[valid], rtol=0, atol=1e-15)
+    p_exp = (float(np.float32(a)) * float(D) ** 2) ** 2
+    assert np.allclose(P[valid], p_exp, rtol=1e-14, atol=0)
+    assert np.isnan(T[invalid]).all()
+
+
+# ----------------------------------------------------------------------------
+# projective measurement T_k (Fusion, last paragraph)
+# ----------------------------------------------------------------------------
+
+def pin_projection_nearest_pixel(lib_path=None):
+    """A voxel reads the pixel nearest to its projection: the depth map encodes
+    each pixel's index, so T + z_c recovers which pixel a voxel used; that pixel's
+    centre must lie within half a pixel of the voxel's projection, computed here
+    with the inverse pose from numpy.linalg.inv."""
+    rng = np.random.default_rng(21)
+    W, H, f = 40, 30, 36.0
+    intr = synth.Intrinsics(f, f * 1.1, 19.3, 14.8, W, H)
+    ang = rng.uniform(-0.3, 0.3, 3)
+    cx_, sx_ = math.cos(ang[0]), math.sin(ang[0])
+    cy_, sy_ = math.cos(ang[1]), math.sin(ang[1])
+    cz_, sz_ = math.cos(ang[2]), math.sin(ang[2])
+    Rx = np.array([[1, 0, 0], [0, cx_, -sx_], [0, sx_, cx_]])
+    Ry = np.array([[cy_, 0, sy_], [0, 1, 0], [-sy_, 0, cy_]])
+    Rz = np.array([[cz_, -sz_, 0], [sz_, cz_, 0], [0, 0, 1]])
+    pose = np.eye(4)
+    pose[:3, :3] = Rz @ Ry @ Rx
+    pose[:3, 3] = rng.uniform(-0.2, 0.2, 3)
+    centre = pose[:3, :3] @ np.array([0.0, 0.0, 1.0]) + pose[:3, 3]
+    s, G = 2e-3, 64
+    vol = synth.VolumeParams(voxel_size=s, truncation=5 * s, origin=tuple(centre - G / 2 * s),
+                             grid_dim=G, block_capacity=4096, depth_min=0.05, depth_max=5.0,
+                             raycast_near=0.05, raycast_far=5.0, sigma_coeff=1e-3)
+    idx = np.arange(W * H).reshape(H, W)
+    depth = (1.0 + 1e-5 * idx).astype(np.float32)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path, amb_px=1e-9)
+    ov.fuse(depth, pose)
+    e = ov.export()
+    vox = oracle.voxel_coords(e)
+    T = e.T.ravel()
+    ok = ~np.isnan(T)
+    assert ok.sum() > 2000, ok.sum()
+    Xw = _voxel_world(vol, vox[ok])
+    inv = np.linalg.inv(pose)
+    Xc = Xw @ inv[:3, :3].T + inv[:3, 3]
+    Dread = T[ok] + Xc[:, 2]
+    k = np.rint((Dread - 1.0) / 1e-5).astype(np.int64)
+    u_read, v_read = k % W, k // W
+    assert np.abs(Dread - depth.ravel()[k]).max() < 1e-9
+    uf = intr.fx * Xc[:, 0] / Xc[:, 2] + intr.cx
+    vf = intr.fy * Xc[:, 1] / Xc[:, 2] + intr.cy
+    assert np.abs(uf - u_read).max() <= 0.5 + 1e-9, np.abs(uf - u_read).max()
+    assert np.abs(vf - v_read).max() <= 0.5 + 1e-9, np.abs(vf - v_read).max()
+    # every voxel whose projection falls inside the image and whose read depth is
+    # within delta must have been updated (no valid measurement is skipped)
+    Xw_all = _voxel_world(vol, vox)
+    Xc_all = Xw_all @ inv[:3, :3].T + inv[:3, 3]
+    ua = np.floor(intr.fx * Xc_all[:, 0] / Xc_all[:, 2] + intr.cx + 0.5)
+    va = np.floor(intr.fy * Xc_all[:, 1] / Xc_all[:, 2] + intr.cy + 0.5)
+    inside = (ua >= 0) & (ua < W) & (va >= 0) & (va < H) & (Xc_all[:, 2] > 0)
+    kk = np.where(inside, va * W + ua, 0).astype(np.int64)
+    Tk = depth.ravel()[kk].astype(np.float64) - Xc_all[:, 2]
+    want = inside & (np.abs(Tk) < vol.truncation * (1 - 1e-6)) & ~e.amb.ravel()
+    assert (ok | ~want).all(), "a voxel with a valid measurement was left chi"
+
+
+# ----------------------------------------------------------------------------
+# allocation (section "Updating Sparse Structure")
+# ----------------------------------------------------------------------------
+
+def pin_alloc_exact_rational(lib_path=None):
+    """The allocated blocks are the blocks holding the surface samples: each valid
+    pixel's ray sampled at D + m delta / J, m = -J..J. Here every sample is placed
+    with exact rational arithmetic (fractions) from the same inputs; a block
+    decision may differ from single precision only for samples within 1e-2 voxel
+    of a block or grid boundary."""
+    rng = np.random.default_rng(31)
+    W, H = 9, 7
+    intr = synth.Intrinsics(7.0, 7.5, 4.2, 2.9, W, H)
+    s, G = 4e-3, 64
+    vol = synth.VolumeParams(voxel_size=s, truncation=5 * s, origin=(-0.13, -0.12, 0.2), grid_dim=G,
+                             block_capacity=100000, depth_min=0.05, depth_max=5.0,
+                             raycast_near=0.05, raycast_far=5.0, sigma_coeff=1e-3)
+    pose = synth.look_at(rng.uniform(-0.05, 0.05, 3), np.array([0.0, 0.0, 0.33]), up=(0.1, 1.0, 0.05))
+    depth = rng.uniform(0.25, 0.45, (H, W)).astype(np.float32)
+    depth[0, 0] = 0.0
+    depth[1, 2] = np.nan
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    keys = set(int(k) for k in ov.frame_blocks(depth, pose))
+    J = ov.half_samples
+    assert J == 10, J
+    nb = G // 8
+    sF, dF = Fraction(float(np.float32(s))), Fraction(float(np.float32(5 * s)))
+    org = [Fraction(o) for o in vol.origin]
+    R = [[Fraction(float(pose[r, c])) for c in range(3)] for r in range(3)]
+    t = [Fraction(float(pose[r, 3])) for r in range(3)]
+    sure, maybe = set(), set()
+    eps = Fraction(1, 100)
+    for j in range(H):
+        for i in range(W):
+            d = float(depth[j, i])
+            if not (d > 0 and math.isfinite(d)):
+                continue
+            xn = (i - Fraction(float(np.float32(intr.cx)))) / Fraction(float(np.float32(intr.fx)))
+            yn = (j - Fraction(float(np.float32(intr.cy)))) / Fraction(float(np.float32(intr.fy)))
+            for m in range(-J, J + 1):
+                z = Fraction(d) + m * dF / J
+                pc = (xn * z, yn * z, z)
+                q = [(sum(R[r][c] * pc[c] for c in range(3)) + t[r] - org[r]) / sF for r in range(3)]
+                cands = []
+                edge = False
+                for r in range(3):
+                    fl = math.floor(q[r])
+                    opts = {fl}
+                    if q[r] - fl < eps:
+                        opts.add(fl - 1)
+                    if fl + 1 - q[r] < eps:
+                        opts.add(fl + 1)
+                    cands.append(opts)
+                    blocks = {o // 8 for o in opts if 0 <= o < G}
+                    if len(blocks) != 1 or len({o for o in opts}) != len([o for o in opts if 0 <= o < G]):
+                        edge = True
+                blist = {(a // 8, b // 8, c // 8) for a in cands[0] for b in cands[1] for c in cands[2]
+                         if 0 <= a < G and 0 <= b < G and 0 <= c < G}
+                kl = {bx + nb * (by + nb * bz) for bx, by, bz in blist}
+                if not edge and len(kl) == 1:
+                    sure |= kl
+                maybe |= kl
+    assert len(sure) > 20, len(sure)
+    assert sure <= keys, sorted(sure - keys)[:10]
+    assert keys <= maybe, sorted(keys - maybe)[:10]
+
+
+def pin_alloc_capacity_and_order(lib_path=None):
+    """A pool with room for only part of a frame's blocks keeps the lowest keys
+    (ascending key order), flags the overflow, and a repeated frame adds nothing."""
+    rng = np.random.default_rng(41)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    vol = _plane_volume(cap=100000)
+    depth = (0.5 + rng.uniform(-0.01, 0.01, (24, 32))).astype(np.float32)
+    full = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    keys = full.frame_blocks(depth, np.eye(4))
+    n_new, over = full.allocate(depth, np.eye(4), 0)
+    assert n_new == len(keys) and not over
+    assert full.allocate(depth, np.eye(4), 1) == (0, False)
+    cap = len(keys) // 3
+    small = oracle.OracleVolume(synth.VolumeParams(**{**vol.__dict__, "block_capacity": cap}), intr,
+                                lib_path=lib_path)
+    n_new, over = small.allocate(depth, np.eye(4), 0)
+    assert n_new == cap and over
+    e = small.export(values=False)
+    nb = vol.grid_dim // 8
+    got = e.coords[:, 0] + nb * (e.coords[:, 1] + nb * e.coords[:, 2])
+    assert np.array_equal(np.sort(got), np.sort(keys)[:cap])
+
+
+def pin_dense_equals_sparse(lib_path=None):
+    """Dense brute force (Alg. 3 on every voxel of the grid) and the sparse volume
+    agree on every voxel of every block allocated at the first frame, and the
+    blocks the sampling misses hold almost no valid voxels."""
+    seq = synth.sphere_sequence(n_frames=4, noise=True, grid_dim=128, voxel_size=2e-3)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, lib_path=lib_path)
+    dn = oracle.DenseOracle(seq.volume, seq.intr)
+    if lib_path is not None:
+        dn.lib = oracle.lib(lib_path)
+        dn.h = dn.lib.ov_dense_create(oracle.ctypes.byref(dn.params))
+    for k in range(seq.n_frames):
+        ov.fuse(seq.depth[k], seq.poses[k])
+        dn.integrate(seq.depth[k], seq.poses[k])
+    e = ov.export()
+    vox = oracle.voxel_coords(e)
+    Td, Pd, _ = dn.read(vox)
+    m = np.repeat(e.alloc_frame == 0, 512)
+    Ts, Ps = e.T.ravel(), e.P.ravel()
+    assert np.array_equal(np.isnan(Ts[m]), np.isnan(Td[m]))
+    ok = m & ~np.isnan(Ts)
+    assert ok.sum() > 10000
+    assert np.array_equal(Ts[ok], Td[ok]) and np.array_equal(Ps[ok], Pd[ok])
+    n_valid, n_missed = dn.coverage(ov)
+    assert n_valid > 10000 and n_missed / n_valid < 0.02, (n_valid, n_missed)
+
+
+# ----------------------------------------------------------------------------
+# raycast (section "Scene Rendering")
+# ----------------------------------------------------------------------------
+
+def pin_plane_raycast_exact(lib_path=None):
+    """A fronto-parallel plane seen by cameras with identity rotation gives
+    T = d0 - z at every voxel, an affine field that trilinear interpolation
+    reproduces exactly: the raycast depth equals d0 - t_z, the vertex lies on the
+    plane and the normal is (0, 0, -1)."""
+    d0 = 0.5
+    vol = _plane_volume(sigma=1e-3)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    poses = []
+    for k in range(3):
+        T = np.eye(4)
+        T[:3, 3] = [0.004 * k, -0.003 * k, 0.002 * k]
+        poses.append(T)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    for T in poses:
+        ov.fuse(np.full((24, 32), d0 - T[2, 3], np.float32), T)
+    Tq = np.eye(4)
+    Tq[:3, 3] = [0.001, 0.002, 0.01]
+    depth, vert, nrm, flags = ov.raycast(Tq)
+    hit = (flags & 1) > 0
+    assert hit.sum() > 40, hit.sum()
+    # frame k measured the plane at world z = D_k + t_z with variance (a D_k^2)^2;
+    # the fused zero level is their inverse-variance weighted mean (Alg. 3, Q = 0)
+    Dk = np.array([float(np.float32(d0 - T[2, 3])) for T in poses])
+    planes = Dk + np.array([T[2, 3] for T in poses])
+    w = 1.0 / (float(np.float32(1e-3)) * Dk ** 2) ** 2
+    plane = float((planes * w).sum() / w.sum())
+    assert np.allclose(depth[hit], plane - Tq[2, 3], atol=1e-9, rtol=0), np.abs(depth[hit] - (plane - Tq[2, 3])).max()
+    assert np.allclose(vert[hit, 2], plane, atol=1e-9)
+    ok = (flags & 4) == 0
+    assert (hit & ok).sum() > 20
+    assert np.allclose(nrm[hit & ok], [0.0, 0.0, -1.0], atol=1e-9)
+    assert np.isnan(vert[~hit]).all() and (depth[~hit] == 0).all()
+
+
+def pin_sphere_raycast_analytic(lib_path=None):
+    """Fusing noise-free views of a sphere and raycasting gives the analytic
+    ray-sphere depth up to the error of the projective distance (the measured
+    depth is constant over a pixel's footprint): within 0.5 voxel where the
+    surface faces the camera (cos > 0.9) and 1.5 voxel at cos > 0.5."""
+    seq = synth.sphere_sequence(noise=False, keep_clean=True)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, lib_path=lib_path)
+    _fuse(ov, seq.depth, seq.poses)
+    pose = seq.poses[-1]
+    d, v, n, fl = ov.raycast(pose)
+    H, W = seq.intr.height, seq.intr.width
+    d = d.reshape(H, W)
+    hit = (fl & 1).reshape(H, W) > 0
+    gt = seq.clean_depth[-1]
+    o, dw = synth._pixel_rays(seq.intr, pose, "cpu")
+    dw = dw.numpy()
+    with np.errstate(invalid="ignore"):
+        P = o.numpy() + gt[..., None] * dw
+        nrm = P / np.linalg.norm(P, axis=-1, keepdims=True)
+        cosv = np.abs((nrm * dw).sum(-1)) / np.linalg.norm(dw, axis=-1)
+    s = seq.volume.voxel_size
+    assert abs(int(hit.sum()) - int(np.isfinite(gt).sum())) < 0.03 * np.isfinite(gt).sum()
+    err = np.abs(d - gt) / s
+    m9 = hit & np.isfinite(gt) & (cosv > 0.9)
+    m5 = hit & np.isfinite(gt) & (cosv > 0.5)
+    assert m9.sum() > 300 and m5.sum() > 1500
+    assert err[m9].max() < 0.5 and err[m9].mean() < 0.1, (err[m9].max(), err[m9].mean())
+    assert err[m5].max() < 1.5, err[m5].max()
+    nn = n.reshape(H, W, 3)
+    good = m9 & np.isfinite(nn[..., 0])
+    ang = np.degrees(np.arccos(np.clip((nn[good] * nrm[good]).sum(-1), -1.0, 1.0)))
+    # the per-pixel staircase of the projective distance tilts the gradient by a
+    # few degrees; a wrong sign or axis would be off by tens of degrees
+    assert np.median(ang) < 6.0 and ang.max() < 15.0, (np.median(ang), ang.max())
+
+
+ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
+            pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
+            pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
+            pin_plane_raycast_exact, pin_sphere_raycast_analytic]
+
+
+def run_all(lib_path=None) -> list:
+    """Names of the pins that fail for the library at ``lib_path``."""
+    failed = []
+    for pin in ALL_PINS:
+        try:
+            pin(lib_path)
+        except AssertionError:
+            failed.append(pin.__name__)
+    return failed

@@ -1,0 +1,79 @@
+"""Plant plausible mistakes in copies of the oracle and check that the pins catch
+each one: evidence that the pins constrain every part of the oracle.
+
+Each mutation is a textual edit of ``oracle/tsdf_oracle.cpp`` compiled into a
+temporary library; the pins run against it in a child process (so a mutation that
+crashed would fail the child, not this test run). The real oracle is untouched.
+"""
+import concurrent.futures
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, text in the oracle, planted replacement)
+MUTATIONS = [
+    ("kalman_correct_sign", "T = T + K * (Tk - T);", "T = T + K * (T - Tk);"),
+    ("kalman_variance_shrink", "P = (1.0 - K) * P;", "P = K * P;"),
+    ("kalman_predict_sign", "P = P + Q;                    // predict", "P = P - Q;"),
+    ("kalman_gain", "const double K = P / (P + pk);", "const double K = pk / (P + pk);"),
+    ("first_measurement_variance", "T = Tk;\n        P = pk;", "T = Tk;\n        P = pk * pk;"),
+    ("camera_rotation_transposed",
+     "xc[k] = f.R[0][k] * d[0] + f.R[1][k] * d[1] + f.R[2][k] * d[2];",
+     "xc[k] = f.R[k][0] * d[0] + f.R[k][1] * d[1] + f.R[k][2] * d[2];"),
+    ("tk_sign", "const double Tk = Dd - z;", "const double Tk = z - Dd;"),
+    ("pixel_floor_not_round", "const double u0 = std::floor(uf + 0.5), v0 = std::floor(vf + 0.5);",
+     "const double u0 = std::floor(uf), v0 = std::floor(vf);"),
+    ("pixel_index_uv_swapped", "const int64_t pix = (int64_t)v * f.in.width + (int64_t)u;",
+     "const int64_t pix = (int64_t)u * f.in.height + (int64_t)v;"),
+    ("truncation_doubled", "if (std::fabs(Tk) > delta) return m;", "if (std::fabs(Tk) > 2.0 * delta) return m;"),
+    ("variance_is_sigma", "pk = sigma * sigma;", "pk = sigma;"),
+    ("voxel_centre_offset", "p.origin[2] + (double)iz * s};", "p.origin[2] + ((double)iz + 0.5) * s};"),
+    ("alloc_rotation_transposed", "c.Mr[r][k] = (float)(pose[4 * r + k] / s);",
+     "c.Mr[r][k] = (float)(pose[4 * k + r] / s);"),
+    ("alloc_half_samples", "std::ceil(2.0 * delta / s - 1e-6)", "std::ceil(0.5 * delta / s - 1e-6)"),
+    ("alloc_block_axes_swapped", "block_key(vx / M, vy / M, vz / M, nb)", "block_key(vy / M, vx / M, vz / M, nb)"),
+    ("alloc_origin_sign", "c.a[r] = (float)((pose[4 * r + 3] - p.origin[r]) / s);",
+     "c.a[r] = (float)((pose[4 * r + 3] + p.origin[r]) / s);"),
+    ("alloc_order_descending", "for (uint32_t key : keys) {",
+     "for (auto it_ = keys.rbegin(); it_ != keys.rend(); ++it_) { const uint32_t key = *it_;"),
+    ("trilinear_weight_swapped", "const double w = (dx ? fr[0] : 1.0 - fr[0])",
+     "const double w = (dx ? 1.0 - fr[0] : fr[0])"),
+    ("raycast_crossing_reversed", "if (f_prev > 0.0 && f <= 0.0) {", "if (f_prev < 0.0 && f >= 0.0) {"),
+    ("normal_orientation", "> 0.0 ? -1.0 : 1.0;", "> 0.0 ? 1.0 : -1.0;"),
+    ("ray_direction_transposed",
+     "d[r] = pose[4 * r] * dc[0] + pose[4 * r + 1] * dc[1] + pose[4 * r + 2] * dc[2];",
+     "d[r] = pose[r] * dc[0] + pose[4 + r] * dc[1] + pose[8 + r] * dc[2];"),
+    ("normal_axis_permuted", "pp[r] += s;\n        pm[r] -= s;",
+     "pp[(r + 1) % 3] += s;\n        pm[(r + 1) % 3] -= s;"),
+]
+
+
+@pytest.fixture(scope="module")
+def variants(tmp_path_factory):
+    src = oracle.source_text()
+    d = tmp_path_factory.mktemp("oracle_mutants")
+    jobs = {}
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for name, old, new in MUTATIONS:
+            assert src.count(old) == 1, f"mutation {name}: anchor text not found once"
+            jobs[name] = ex.submit(oracle.compile_variant, src.replace(old, new), str(d / f"lib_{name}.so"))
+        return {k: v.result() for k, v in jobs.items()}
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(variants, name):
+    code = ("import sys, json; sys.path.insert(0, %r); sys.path.insert(0, %r); import pins; "
+            "print(json.dumps(pins.run_all(%r)))" % (ROOT, os.path.join(ROOT, "tests"), variants[name]))
+    env = dict(os.environ, OMP_NUM_THREADS=str(min(8, os.cpu_count() or 1)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+    if r.returncode != 0:
+        return      # the planted mistake crashed the oracle: caught
+    failed = json.loads(r.stdout.strip().splitlines()[-1])
+    assert failed, f"no pin caught the planted mistake {name}"
