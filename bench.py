@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark of live sparse TSDF fusion on the room-scale workload.
+
+Workload: ground plane + 50 seeded spheres/boxes in a 3 m room, 640x480 depth
+maps (fx = fy = 525) along a 300-frame seeded spline, noise sigma = 1.5e-3 z^2
+plus 2 % edge dropout, fused into a 2048^3 grid of 1.5 mm voxels (truncation
+7.5 mm, pool of 2^20 8^3-voxel blocks), float32 T and P.
+
+One step = one pass of the whole hot path over the sequence: reset the volume,
+then for each frame allocate -> integrate (Alg. 3) -> raycast at the frame's
+pose. ``value`` is frames fused per second over all ranks (each rank fuses its
+own replica: weak scaling), inputs resident in HBM. ``e2e`` is the same through
+the public Python API with each depth map copied from pinned host memory and
+the last raycast maps read back every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (plain FP64 C++, all host cores) on a
+bounded sample of the same workload and prints the same JSON line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "room-scale plain FP32: 640x480, 2048^3 grid of 1.5 mm voxels, 300 frames"
+METRIC, UNIT = "frames/s", "frames/s"
+LAUNCHES_PER_FRAME = 13    # allocate 5 + integrate 3 + raycast 5 kernels
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block-capacity", type=int, default=1 << 20, help="pool size in blocks")
+    ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
+    ap.add_argument("--cpu-ray-stride", type=int, default=8, help="oracle sample: pixel stride per axis")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (the reported CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(seq, frames, stride, ov=None, start=0):
+    """Time the oracle fusing ``frames`` frames (allocate + Alg. 3 over every
+    allocated block) and raycasting every ``stride``-th pixel per axis; returns
+    (seconds per full frame, the oracle volume)."""
+    import numpy as np
+    import oracle
+    if ov is None:
+        ov = oracle.OracleVolume(seq.volume, seq.intr)
+    t_fuse = t_ray = 0.0
+    H, W = seq.intr.height, seq.intr.width
+    vv, uu = np.meshgrid(np.arange(0, H, stride), np.arange(0, W, stride), indexing="ij")
+    uv = np.stack([uu.ravel(), vv.ravel()], -1)
+    scale = (H * W) / uv.shape[0]
+    for k in range(start, start + frames):
+        f = k % seq.n_frames
+        t0 = time.perf_counter()
+        ov.fuse(seq.depth[f], seq.poses[f])
+        t1 = time.perf_counter()
+        ov.raycast(seq.poses[f], uv)
+        t2 = time.perf_counter()
+        t_fuse += t1 - t0
+        t_ray += (t2 - t1) * scale
+    return (t_fuse + t_ray) / frames, ov
+
+
+def make_sequence(n_frames, device, block_capacity=1 << 20):
+    from paper_1311_7194_b300 import synth
+    return synth.room_sequence(seed=1, n_frames=n_frames, device=device, block_capacity=block_capacity)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    frames_per_step = 1
+    seq = make_sequence(max(1, min(args.frames, (args.warmup + args.steps) * frames_per_step)), "cpu")
+    ov = None
+    k = 0
+    for _ in range(args.warmup):
+        _, ov = oracle_sample(seq, frames_per_step, args.cpu_ray_stride, ov, start=k)
+        k += frames_per_step
+    per = []
+    for _ in range(args.steps):
+        t, ov = oracle_sample(seq, frames_per_step, args.cpu_ray_stride, ov, start=k)
+        k += frames_per_step
+        per.append(t)
+    sec = sum(per) / len(per)
+    value = 1.0 / sec
+    cores = oracle.num_threads()
+    sample = (f"each step: oracle fuses 1 full 640x480 frame (allocate + Alg. 3 over every allocated "
+              f"block, FP64) and raycasts every {args.cpu_ray_stride}th pixel per axis, scaled to the full "
+              f"frame; frames {args.warmup}..{k - 1} of the sequence after {args.warmup} warm-up frames")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# DRAM traffic of the integrate stage measured by ncu on this workload, per
+# voxel update (dram__bytes_read.sum + dram__bytes_write.sum over the stage's
+# kernels / voxel updates), with the source hash it was measured on; the value is
+# dropped when the kernel source changes.
+NCU_TRAFFIC = {"integrate": None}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1311_7194_b300 import build as pkg_build
+    from paper_1311_7194_b300 import tsdf
+    from paper_1311_7194_b300.pipeline import FusionPipeline
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        pkg_build.build()
+    if world > 1:
+        dist.barrier()
+    tsdf.load()
+
+    seq = make_sequence(args.frames, dev, args.block_capacity)
+    F, H, W = seq.depth.shape
+    depth_dev = torch.from_numpy(seq.depth).to(dev)
+    vol = tsdf.Volume.from_params(seq.volume)
+    pipe = FusionPipeline(vol, seq.intr, dev)
+    stream = torch.cuda.current_stream()
+
+    def step(stage_events=None):
+        vol.reset()
+        for k in range(F):
+            if stage_events is None:
+                pipe.step(depth_dev[k], seq.poses[k])
+            else:
+                e = stage_events[k]
+                e[0].record(stream)
+                vol.allocate(depth_dev[k], seq.intr, seq.poses[k])
+                e[1].record(stream)
+                vol.integrate(depth_dev[k], seq.intr, seq.poses[k])
+                e[2].record(stream)
+                vol.raycast(seq.intr, seq.poses[k], out=pipe.maps)
+                e[3].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    vol.check()
+
+    # timed region: whole steps bracketed by barrier + synchronize
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(F)] for _ in range(args.steps)]
+    t0.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1000.0
+    st = vol.stats()
+    vol.check()
+    stage = np.zeros(3)
+    for s in range(args.steps):
+        for k in range(F):
+            e = ev[s][k]
+            stage += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+    stage_ms_per_step = stage / args.steps
+
+    t_max = torch.tensor([elapsed], device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t_max.item())
+    frames_total = F * args.steps * world
+    value = frames_total / elapsed_max
+    updates_per_step = st["voxel_updates_total"]
+    rays_per_step = F * H * W
+
+    # per-frame work counts (one extra, untimed step, synchronising per frame)
+    vol.reset()
+    n_blocks, visible, updates = [], [], []
+    for k in range(F):
+        vol.allocate(depth_dev[k], seq.intr, seq.poses[k])
+        vol.integrate(depth_dev[k], seq.intr, seq.poses[k])
+        s_ = vol.stats()
+        n_blocks.append(s_["n_blocks"]); visible.append(s_["visible_blocks"]); updates.append(s_["voxel_updates"])
+    n_blocks, visible, updates = map(np.asarray, (n_blocks, visible, updates))
+    # integrate stage, algorithmic bytes per frame: read+write T and P of every
+    # updated voxel (16 B), the depth map (4 B/px), the block list read by the
+    # cull (16 B/block) and the visible list written and read (32 B each way)
+    integ_bytes = 16.0 * updates + 4.0 * H * W + 16.0 * n_blocks + 64.0 * visible
+    integ_sec = stage_ms_per_step[1] / 1000.0
+    peak, peak_kind = peaks()
+    achieved = integ_bytes.sum() / integ_sec / 1e9
+    integ_src = os.path.join(ROOT, "paper_1311_7194_b300", "csrc", "tsdf_integrate.cu")
+    traffic = None
+    rec = NCU_TRAFFIC.get("integrate")
+    if rec and rec.get("sha") == _sha(integ_src):
+        traffic = rec["bytes_per_update"] * float(updates.mean())
+    roofline = {"kernel": "integrate stage (cull + Alg. 3 integrate), per frame", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": float(integ_bytes.mean()),
+                "avg_launch_ms": 1000.0 * integ_sec / F}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded analytic room scene, quadratic depth noise, edge dropout",
+            "config": {"workload": WORKLOAD, "frames_per_step": F, "width": W, "height": H, "grid_dim": 2048,
+                       "voxel_size_m": 1.5e-3, "block_capacity": args.block_capacity, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step"},
+            "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,
+            "rays_per_s": rays_per_step * args.steps * world / elapsed_max,
+            "stage_ms_per_step": {"allocate": stage_ms_per_step[0], "integrate": stage_ms_per_step[1],
+                                  "raycast": stage_ms_per_step[2]},
+            "work_per_step": {"voxel_updates": int(updates_per_step), "blocks": int(st["n_blocks"]),
+                              "visible_blocks": int(st["visible_blocks_total"]),
+                              "rays_hit": int(st["rays_hit_total"])},
+            "roofline": roofline,
+            "gpu_launches": LAUNCHES_PER_FRAME * F * args.steps,
+            "clocks": clk}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        host = torch.from_numpy(seq.depth).pin_memory()
+        out_host = [torch.empty(m.shape, dtype=torch.float32).pin_memory() for m in pipe.maps]
+        for _ in range(1):
+            vol.reset()
+            for k in range(F):
+                pipe.step_host(host[k], seq.poses[k])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            vol.reset()
+            for k in range(F):
+                pipe.step_host(host[k], seq.poses[k])
+            for o, m in zip(out_host, pipe.maps):
+                o.copy_(m, non_blocking=True)
+            vol.stats()     # synchronises and reads the step's counters
+        torch.cuda.synchronize()
+        e2e_sec = time.perf_counter() - w0
+        te = torch.tensor([e2e_sec], device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": frames_total / float(te.item()), "unit": UNIT,
+                       "h2d_bytes_per_step": int(F * H * W * 4),
+                       "d2h_bytes_per_step": int(28 * H * W + 11 * 8)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sec, _ = oracle_sample(seq, args.cpu_frames, args.cpu_ray_stride)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"oracle fuses the first {args.cpu_frames} frames at 640x480 (allocate + "
+                                          f"Alg. 3 over every allocated block, FP64) and raycasts every "
+                                          f"{args.cpu_ray_stride}th pixel per axis, scaled to full frames"}
+    vol.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

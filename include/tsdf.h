@@ -1,0 +1,204 @@
+/*
+ * tsdf.h - C ABI of the B300 sparse TSDF fusion library (libtsdf.so).
+ *
+ * The library implements the data-parallel hot path of Trifonov, "Real-time High
+ * Resolution Fusion of Depth Maps on GPU" (arXiv 1311.7194):
+ *   1. allocation of the 8^3-voxel blocks that a posed depth map's surface
+ *      touches (section "Updating Sparse Structure"),
+ *   2. per-voxel Kalman update of distance T and variance P (Alg. 3) from the
+ *      projective measurement T_k (section "Integration of Measurements"),
+ *   3. raycasting of the sparse TSDF into depth, normal and vertex maps
+ *      (section "Scene Rendering": block-range maps, coarse march, refinement).
+ *
+ * Conventions used by every call
+ *   - Lengths in metres. Camera: pinhole with OpenCV axes (x right, y down,
+ *     z forward); pixel (u, v) has its centre at integer coordinates and
+ *     u = fx * x / z + cx.
+ *   - Poses are camera-to-world 4x4 matrices T_wc, row major, 16 doubles in
+ *     HOST memory, last row (0 0 0 1).
+ *   - Voxel index i (3 integers in [0, grid_dim)) sits at world position
+ *     origin + i * voxel_size. Block b = floor(i / 8); the voxel's index inside
+ *     its block is x + 8 y + 64 z of i mod 8.
+ *   - Images (depth, variance, output maps) are DEVICE pointers owned by the
+ *     caller, float32, row major, width * height elements (x3 interleaved for
+ *     normal/vertex maps). Depth 0, negative, NaN, Inf or outside
+ *     [depth_min, depth_max] means "no measurement" (the paper's chi).
+ *   - Every compute call is asynchronous on the given stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream) and does not synchronise.
+ *     Argument errors are returned at once; errors found on the device
+ *     (pool exhausted) set a sticky flag that tsdf_get_status reports.
+ *   - A volume is not thread safe: serialise calls on one volume.
+ *   - No call aborts the process or traps the GPU.
+ */
+#ifndef TSDF_H
+#define TSDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsdf_volume tsdf_volume; /* opaque; owned by the library */
+
+typedef enum {
+    TSDF_OK = 0,
+    TSDF_ERR_INVALID_ARG = 1,   /* null pointer, bad size or non-finite parameter */
+    TSDF_ERR_CAPACITY = 2,      /* pool full: some new blocks were not allocated */
+    TSDF_ERR_HASH_FULL = 3,     /* reserved: the dense block table never fills */
+    TSDF_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+    TSDF_ERR_NOT_READY = 5,     /* reserved */
+    TSDF_ERR_OUT_OF_MEMORY = 6  /* device allocation failed in tsdf_create* */
+} tsdf_status;
+
+typedef enum {
+    TSDF_STORAGE_F32 = 0        /* T stored as float32, chi = NaN */
+} tsdf_storage;
+
+/* Pinhole intrinsics of one depth map / output map. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} tsdf_intrinsics;
+
+/* Volume settings (tsdf_config_default fills the defaults named below). */
+typedef struct {
+    float voxel_size;           /* s > 0 (default 1.5e-3) */
+    float truncation;           /* delta > 0, Eq. 1 (default 5 s) */
+    double origin[3];           /* world position of voxel (0,0,0)
+                                   (default -grid_dim*s/2 on every axis) */
+    int32_t grid_dim;           /* G voxels per axis, multiple of 8, (G/8)^3 < 2^32
+                                   (default 2048) */
+    int64_t block_capacity;     /* pool size in blocks (default 2^20) */
+    float process_variance;     /* Q >= 0 of Alg. 3 (default 0) */
+    float depth_min, depth_max; /* valid measured depth range (default 0.1 .. 4) */
+    float raycast_near, raycast_far; /* raycast depth range (default 0.1 .. 4) */
+    float sigma_coeff;          /* a >= 0: sensor deviation a*D^2, used when no
+                                   variance map is given (default 1.5e-3) */
+    int32_t storage;            /* tsdf_storage (default TSDF_STORAGE_F32) */
+    int32_t alloc_half_samples; /* J >= 0; 0 = ceil(2 delta / s) (default 0) */
+} tsdf_config;
+
+/* Counters of the last calls (tsdf_get_stats). */
+typedef struct {
+    int64_t n_blocks;           /* blocks in the pool */
+    int64_t new_blocks;         /* blocks added by the last tsdf_allocate */
+    int64_t visible_blocks;     /* blocks the last tsdf_integrate visited */
+    int64_t voxel_updates;      /* voxels updated (T_k != chi) by the last tsdf_integrate */
+    int64_t raycast_blocks;     /* blocks rasterised by the last tsdf_raycast */
+    int64_t rays_hit;           /* pixels that found a surface in the last tsdf_raycast */
+    int64_t frames;             /* tsdf_integrate calls since creation / reset */
+    int64_t voxel_updates_total;   /* sums over all calls since creation / reset */
+    int64_t visible_blocks_total;
+    int64_t rays_hit_total;
+    int64_t raycast_blocks_total;
+} tsdf_stats;
+
+/* Fill *cfg with the defaults listed in tsdf_config. Host only. */
+void tsdf_config_default(tsdf_config* cfg);
+
+/* Human-readable name of a status code (static string). */
+const char* tsdf_status_string(tsdf_status s);
+
+/* Create an empty volume with the given voxel size, truncation and pool
+ * capacity, all other settings at their defaults (section "Volumetric Scene
+ * Representation": two device buffers, a block table and a pool of M^3-voxel
+ * blocks, here M = 8). Allocates device memory on the current CUDA device:
+ * 4 (G/8)^3 bytes of block table plus 8*512 bytes per pool block plus small
+ * lists. *out receives the handle, to be freed with tsdf_destroy.
+ * Errors: TSDF_ERR_INVALID_ARG (bad values, out == NULL),
+ *         TSDF_ERR_OUT_OF_MEMORY, TSDF_ERR_CUDA. */
+tsdf_status tsdf_create(float voxel_size, float truncation, int64_t block_capacity,
+                        tsdf_volume** out);
+
+/* Same with every setting given. Errors as tsdf_create. */
+tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out);
+
+/* Free a volume and its device memory (synchronises its last stream). NULL is
+ * a no-op. */
+void tsdf_destroy(tsdf_volume* vol);
+
+/* Empty the volume (no blocks, frame counter 0, status cleared) without freeing
+ * memory; asynchronous on stream. */
+tsdf_status tsdf_reset(tsdf_volume* vol, void* stream);
+
+/* Allocate the blocks one posed depth map's surface touches (section "Updating
+ * Sparse Structure"; the paper samples the surface, writes block coordinates
+ * and allocates them, missing a few blocks being tolerable). Every valid pixel
+ * (i, j) is sampled at 2J+1 depths D + m delta/J, m = -J..J, along its ray; the
+ * block of each sample inside the grid is allocated if it is not yet. New blocks
+ * of one call join the pool in ascending key order (key = bx + N (by + N bz),
+ * N = G/8), hold chi everywhere and remember the frame counter as their
+ * allocation frame. The sample arithmetic is a fixed sequence of correctly
+ * rounded float32 operations, so the block set is reproducible bit for bit:
+ *   xn = (i - cx)/fx, yn = (j - cy)/fy; b = fma(M0, xn, fma(M1, yn, M2)) per row
+ *   of M = R/s; z_m = fma(m, delta/J, D); q = fma(z_m, b, (t - origin)/s);
+ *   inside iff 0 <= q < G; block = floor(q) / 8,
+ * with M, delta/J and (t - origin)/s computed in double and rounded once.
+ * depth: device, width*height float32. K: host. pose_wc: host, 16 doubles.
+ * When the pool is full, the highest-key new blocks are dropped and the sticky
+ * status TSDF_ERR_CAPACITY is set. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_allocate(tsdf_volume* vol, const float* depth, const tsdf_intrinsics* K,
+                          const double pose_wc[16], void* stream);
+
+/* Fuse one posed depth map into the allocated blocks with Alg. 3. For every
+ * voxel x of every allocated block: x_c = T_wc^-1 x; pixel = nearest
+ * (floor(fx x_c/z_c + cx + 1/2), same for v); T_k = D(pixel) - z_c (the
+ * projective distance, positive in front of the surface, Eq. 1), chi when
+ * z_c <= 0, the pixel is outside the image, D is not valid, p_k is not a
+ * positive finite number, or |T_k| > delta. For T_k != chi:
+ *   T == chi:  T = T_k, P = p_k
+ *   else:      P += Q; K = P/(P+p_k); T += K (T_k - T); P = (1-K) P
+ *   then:      T = chi if |T| > delta.
+ * p_k = variance[pixel] when variance != NULL (device, width*height float32),
+ * else (sigma_coeff * D^2)^2. Only blocks whose box can reach the image and the
+ * depth range are visited (a conservative cull); all other voxels are
+ * unchanged. Increments the frame counter. Errors: TSDF_ERR_INVALID_ARG,
+ * TSDF_ERR_CUDA. */
+tsdf_status tsdf_integrate(tsdf_volume* vol, const float* depth, const float* variance,
+                           const tsdf_intrinsics* K, const double pose_wc[16], void* stream);
+
+/* Raycast the fused surface into depth / normal / vertex maps of size
+ * K->width x K->height (section "Scene Rendering"). Per pixel, a range map made
+ * by rasterising the boxes of the allocated blocks (nearest front / farthest
+ * back, clamped to [raycast_near, raycast_far]) bounds the march; the ray is
+ * marched in camera z with step delta/2 over the trilinear interpolation of T
+ * (undefined where any of the 8 voxels is chi or unallocated; unallocated
+ * blocks are skipped whole) until the first + to - crossing; a - to + crossing
+ * first ends the ray as a miss. The crossing is refined by secant steps.
+ * depth_out: camera z (0 on a miss); vertex_out: world position (NaN on a miss);
+ * normal_out: normalised central-difference gradient of T (+-1 voxel), in world
+ * axes, facing the camera (NaN on a miss or undefined gradient). Any output may
+ * be NULL. Outputs are device pointers (depth: W*H floats, normal/vertex:
+ * W*H*3 floats, xyz interleaved). Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
+                         float* depth_out, float* normal_out, float* vertex_out, void* stream);
+
+/* Per-pixel measurement variance of a sensor whose deviation grows
+ * quadratically with depth (Introduction; the text before Alg. 3):
+ * var[i] = (sigma_coeff * depth[i]^2)^2 for valid depth > 0, else 0.
+ * depth, var_out: device, n float32. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_quadratic_variance(const float* depth, int64_t n, float sigma_coeff,
+                                    float* var_out, void* stream);
+
+/* Synchronise the volume's last stream and return the first error seen:
+ * a sticky device flag (TSDF_ERR_CAPACITY) or a CUDA error. */
+tsdf_status tsdf_get_status(tsdf_volume* vol);
+
+/* Synchronise and copy the counters into *out (host). */
+tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
+
+/* Copy the volume to HOST buffers in pool order (synchronises). For n blocks:
+ * coords_frame: n x 4 int32 (bx, by, bz, allocation frame); T: n x 512 float32
+ * (chi = NaN); P: n x 512 float32 (unspecified where T is chi). Any buffer may
+ * be NULL; capacity is the number of blocks each buffer holds. *n_out receives
+ * the pool size; if it exceeds capacity only the first capacity blocks are
+ * copied. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_export(tsdf_volume* vol, int32_t* coords_frame, float* T, float* P,
+                        int64_t capacity, int64_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSDF_H */

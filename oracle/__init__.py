@@ -91,6 +91,7 @@ def _load(path: Optional[str] = None) -> ctypes.CDLL:
         "ov_dense_read": (None, [_P, ctypes.c_int64, _I32, _D, _D, _U8]),
         "ov_dense_coverage": (None, [_P, _P, _I64, _I64]),
         "ov_num_threads": (ctypes.c_int32, []),
+        "ov_field": (None, [_P, ctypes.c_int64, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +233,14 @@ class OracleVolume:
         self.lib.ov_raycast(self.h, ctypes.byref(it), _ptr(T, _D), n, _ptr(uv, _I32), _ptr(depth, _D),
                             _ptr(vert, _D), _ptr(nrm, _D), _ptr(flags, _I32))
         return depth, vert, nrm, flags
+
+
+    def field(self, points: np.ndarray) -> np.ndarray:
+        """Trilinear field at world points (n, 3); NaN where undefined."""
+        pts = np.ascontiguousarray(points, np.float64).reshape(-1, 3)
+        out = np.empty(pts.shape[0])
+        self.lib.ov_field(self.h, pts.shape[0], _ptr(pts, _D), _ptr(out, _D))
+        return out
 
 
 def replay_voxels(vol, intr, depths: Seq[np.ndarray], poses: np.ndarray, voxels: np.ndarray,

@@ -407,8 +407,30 @@ bool trilinear(const Volume& v, const double p[3], double* out) {
 
 struct RayOut {
     double depth, vertex[3], normal[3];
-    int32_t flags;   // 1 hit, 2 bisection met an undefined sample, 4 normal undefined
+    int32_t flags;   // 1 hit, 2 bisection met an undefined sample, 4 normal undefined,
+                     // 8 crossing not unique within delta/2 (see crossing_unique)
 };
+
+// Whether the ray's sign change at camera depth zc is the only one, and the
+// field is defined throughout, within one coarse step (delta/2) on either side.
+// Where it is not, a march that samples the ray every delta/2 (the two-stage
+// raycast of section "Scene Rendering") may legitimately report another zero
+// crossing close by; such pixels are flagged.
+bool crossing_unique(const Volume& v, const double o[3], const double d[3], double zc, double step) {
+    const double h = 0.5 * (double)v.p.truncation;
+    bool prev_def = false;
+    double f_prev = 0.0;
+    int changes = 0;
+    for (double z = zc - h; z <= zc + h; z += step) {
+        double p[3] = {o[0] + z * d[0], o[1] + z * d[1], o[2] + z * d[2]};
+        double f;
+        if (!trilinear(v, p, &f)) return false;
+        if (prev_def && ((f_prev > 0.0 && f <= 0.0) || (f_prev <= 0.0 && f > 0.0))) ++changes;
+        prev_def = true;
+        f_prev = f;
+    }
+    return changes <= 1;
+}
 
 RayOut cast_ray(const Volume& v, const ov_intr& in, const double* pose, int32_t u, int32_t w) {
     const double nan = std::numeric_limits<double>::quiet_NaN();
@@ -466,7 +488,10 @@ RayOut cast_ray(const Volume& v, const ov_intr& in, const double* pose, int32_t 
                 found = true;
                 break;
             }
-            if (f_prev < 0.0 && f > 0.0) break;   // back face first: miss
+            if (f_prev < 0.0 && f > 0.0) {        // back face first: miss
+                if (!crossing_unique(v, o, d, z, step)) out.flags |= 8;
+                break;
+            }
         }
         prev_def = def;
         f_prev = f;
@@ -486,6 +511,7 @@ RayOut cast_ray(const Volume& v, const ov_intr& in, const double* pose, int32_t 
     }
     const double zs = 0.5 * (zl + zr);
     out.flags |= 1;
+    if (!crossing_unique(v, o, d, zs, step)) out.flags |= 8;
     out.depth = zs;
     double p[3];
     at(zs, p);
@@ -609,6 +635,16 @@ void ov_raycast(const void* h, const ov_intr* in, const double* pose, int64_t n,
             normal[3 * k + c] = r.normal[c];
         }
         flags[k] = r.flags;
+    }
+}
+
+// Trilinear field at n world points (n x 3): value, or NaN where undefined.
+void ov_field(const void* h, int64_t n, const double* points, double* f) {
+    const Volume& v = *static_cast<const Volume*>(h);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        double val;
+        f[k] = trilinear(v, points + 3 * k, &val) ? val : std::numeric_limits<double>::quiet_NaN();
     }
 }
 

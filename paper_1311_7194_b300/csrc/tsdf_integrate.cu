@@ -1,0 +1,234 @@
+// Measurement integration (section "Integration of Measurements", Alg. 3).
+//
+//   cull_kernel:      one thread per allocated block; keeps blocks whose box can
+//                     project into the image within the depth range where a
+//                     voxel can have |T_k| <= delta (a conservative superset of
+//                     dom(T_k), section "Updating Sparse Structure"), and stores
+//                     the camera-space position of the block's first voxel,
+//                     computed in double and split into a float hi/lo pair.
+//   integrate_kernel: persistent CTAs of 128 threads walk the visible list; a
+//                     thread owns 4 consecutive voxels of an x row, so a warp
+//                     covers 128 voxels = 512 contiguous bytes of T and of P.
+//                     Each voxel is projected into the depth map first; only
+//                     voxels with T_k != chi load, update and store T and P
+//                     (float4 per thread), so a warp whose voxels are all out of
+//                     the band touches no pool memory. No atomics inside a block.
+//
+// Precision: at 3 m a float's spacing (2.4e-7 m) exceeds 1e-5 of a 7.5 mm
+// truncation, so z is never formed as one float. T_k = (D - z_hi) - (z_lo + dz):
+// D - z_hi is exact (Sterbenz: both within a factor 2 whenever |T_k| <= delta),
+// z_lo + dz is small, and the result keeps full precision.
+#include "tsdf_internal.cuh"
+
+namespace tsdf {
+namespace {
+
+constexpr int kIntegrateThreads = 128;
+
+__device__ __forceinline__ void cam_block_origin(const FrameParams& p, int4 bc, double o[3]) {
+    const double x = p.origin[0] + (double)(kSide * bc.x) * p.s - p.t[0];
+    const double y = p.origin[1] + (double)(kSide * bc.y) * p.s - p.t[1];
+    const double z = p.origin[2] + (double)(kSide * bc.z) * p.s - p.t[2];
+    // camera coordinates R^T (X - t)
+    o[0] = p.R[0] * x + p.R[3] * y + p.R[6] * z;
+    o[1] = p.R[1] * x + p.R[4] * y + p.R[7] * z;
+    o[2] = p.R[2] * x + p.R[5] * y + p.R[8] * z;
+}
+
+// Conservative visibility of the box spanning voxel offsets [lo, hi] of a block
+// whose voxel (0,0,0) sits at camera position oc: the box must reach the camera
+// depth range [zlo, zhi] and, when entirely in front of the camera, its
+// projection must overlap the image dilated by `pad` pixels.
+__device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc[3], float lo, float hi,
+                                            float zlo, float zhi, float pad, float* zmin_out,
+                                            float* zmax_out, float rect[4]) {
+    float zmin = 3.0e38f, zmax = -3.0e38f;
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float ax = (c & 1) ? hi : lo, ay = (c & 2) ? hi : lo, az = (c & 4) ? hi : lo;
+        const float x = oc[0] + ax * p.cs[0] + ay * p.cs[1] + az * p.cs[2];
+        const float y = oc[1] + ax * p.cs[3] + ay * p.cs[4] + az * p.cs[5];
+        const float z = oc[2] + ax * p.cs[6] + ay * p.cs[7] + az * p.cs[8];
+        zmin = fminf(zmin, z);
+        zmax = fmaxf(zmax, z);
+        const float rz = 1.0f / fmaxf(z, 1e-20f);
+        const float u = p.fx * x * rz + p.cx, v = p.fy * y * rz + p.cy;
+        umin = fminf(umin, u); umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    }
+    *zmin_out = zmin;
+    *zmax_out = zmax;
+    if (zmax < zlo || zmin > zhi) return false;
+    if (zmin <= 1e-6f) {
+        rect[0] = -1e30f; rect[1] = 1e30f; rect[2] = -1e30f; rect[3] = 1e30f;
+        return true;     // the box reaches behind the camera plane: keep it
+    }
+    rect[0] = umin; rect[1] = umax; rect[2] = vmin; rect[3] = vmax;
+    return umax >= -0.5f - pad && umin <= (float)p.width - 0.5f + pad && vmax >= -0.5f - pad &&
+           vmin <= (float)p.height - 0.5f + pad;
+}
+
+__global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
+                                                   FrameParams p, VisibleBlock* __restrict__ vis) {
+    const long long n = ctr->n_blocks;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+        const long long b = b0 + lane;
+        bool keep = false;
+        double o[3];
+        if (b < n) {
+            cam_block_origin(p, blocks[b], o);
+            const float of[3] = {(float)o[0], (float)o[1], (float)o[2]};
+            float zmin, zmax, rect[4];
+            keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (keep) {
+            VisibleBlock e;
+            e.slot = (int)b;
+            for (int r = 0; r < 3; ++r) {
+                e.hi[r] = (float)o[r];
+                e.lo[r] = (float)(o[r] - (double)e.hi[r]);
+            }
+            e.pad = 0;
+            vis[base + __popc(m & ((1u << lane) - 1u))] = e;
+        }
+    }
+}
+
+// Projective measurement T_k of one voxel (Fusion: project x onto the depth map,
+// distance to the measured point; chi when there is no measurement).
+template <bool kVarMap>
+__device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float ly, float lz,
+                                        const float* __restrict__ depth, const float* __restrict__ var,
+                                        float* Tk, float* pk) {
+    const float dx = __fmaf_rn(lx, p.cs[0], __fmaf_rn(ly, p.cs[1], __fmul_rn(lz, p.cs[2])));
+    const float dy = __fmaf_rn(lx, p.cs[3], __fmaf_rn(ly, p.cs[4], __fmul_rn(lz, p.cs[5])));
+    const float dz = __fmaf_rn(lx, p.cs[6], __fmaf_rn(ly, p.cs[7], __fmul_rn(lz, p.cs[8])));
+    const float zs = __fadd_rn(vb.lo[2], dz);
+    const float z = __fadd_rn(vb.hi[2], zs);
+    if (!(z > 0.0f)) return false;
+    const float x = __fadd_rn(vb.hi[0], __fadd_rn(vb.lo[0], dx));
+    const float y = __fadd_rn(vb.hi[1], __fadd_rn(vb.lo[1], dy));
+    const float uf = __fmaf_rn(p.fx, __fdiv_rn(x, z), p.cxh);   // u + 1/2
+    const float vf = __fmaf_rn(p.fy, __fdiv_rn(y, z), p.cyh);
+    if (!(uf >= 0.0f && uf < (float)p.width && vf >= 0.0f && vf < (float)p.height)) return false;
+    const int pix = (int)floorf(vf) * p.width + (int)floorf(uf);
+    const float D = __ldg(depth + pix);
+    if (!depth_ok(D, p.depth_min, p.depth_max)) return false;
+    float pv;
+    if (kVarMap) {
+        pv = __ldg(var + pix);
+    } else {
+        const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, D), D);
+        pv = __fmul_rn(sg, sg);
+    }
+    if (!(pv > 0.0f && pv <= 3.0e38f)) return false;
+    const float t = __fsub_rn(__fsub_rn(D, vb.hi[2]), zs);
+    if (!(fabsf(t) <= p.delta)) return false;
+    *Tk = t;
+    *pk = pv;
+    return true;
+}
+
+// Alg. 3 for one voxel: chi is NaN.
+__device__ __forceinline__ void kalman(float& T, float& P, float Tk, float pk, float Q, float delta) {
+    if (isnan(T)) {
+        T = Tk;
+        P = pk;
+    } else {
+        P = __fadd_rn(P, Q);                              // predict
+        const float K = __fdiv_rn(P, __fadd_rn(P, pk));   // gain
+        T = __fmaf_rn(K, __fsub_rn(Tk, T), T);            // correct
+        P = __fmul_rn(__fsub_rn(1.0f, K), P);
+    }
+    if (fabsf(T) > delta) T = __int_as_float(0x7fc00000);
+}
+
+template <bool kVarMap>
+__global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* __restrict__ ctr,
+                                                                      const VisibleBlock* __restrict__ vis,
+                                                                      float* __restrict__ T, float* __restrict__ P,
+                                                                      const float* __restrict__ depth,
+                                                                      const float* __restrict__ var, FrameParams p) {
+    const unsigned nvis = ctr->n_visible;
+    const int v0 = threadIdx.x * 4;                       // first of this thread's 4 voxels
+    const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
+    unsigned updates = 0;
+    for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
+        const VisibleBlock vb = vis[i];
+        float tk[4], pk[4];
+        bool ok[4];
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, ly, lz, depth, var, &tk[e], &pk[e]);
+            any |= ok[e];
+        }
+        if (!any) continue;
+        const size_t off = (size_t)vb.slot * kBlockVoxels + (size_t)v0;
+        float4 t4 = *reinterpret_cast<const float4*>(T + off);
+        float4 p4 = *reinterpret_cast<const float4*>(P + off);
+        float tv[4] = {t4.x, t4.y, t4.z, t4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (ok[e]) {
+                kalman(tv[e], pv[e], tk[e], pk[e], p.Q, p.delta);
+                ++updates;
+            }
+        }
+        *reinterpret_cast<float4*>(T + off) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+        *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    }
+    updates = warp_sum(updates);
+    if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+}
+
+__global__ void reset_frame_counters(Counters* ctr) {
+    ctr->updates_total += ctr->voxel_updates;
+    ctr->visible_total += ctr->n_visible;
+    ctr->n_visible = 0;
+    ctr->voxel_updates = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
+                             cudaStream_t st) {
+    reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
+    cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible);
+    const unsigned grid = (unsigned)v->num_sms * 12;
+    if (var)
+        integrate_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
+    else
+        integrate_kernel<false><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
+    return cudaGetLastError();
+}
+
+__global__ void quadratic_variance_kernel(const float* __restrict__ depth, long long n, float a,
+                                          float* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = depth[i];
+        float r = 0.0f;
+        if (isfinite(d) && d > 0.0f) {
+            const float sg = __fmul_rn(__fmul_rn(a, d), d);
+            r = __fmul_rn(sg, sg);
+        }
+        out[i] = r;
+    }
+}
+
+cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    quadratic_variance_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(depth, n, a, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tsdf

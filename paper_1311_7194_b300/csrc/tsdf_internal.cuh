@@ -1,0 +1,126 @@
+// Internal declarations of libtsdf: device data layout, per-call constants and
+// the launchers each stage file provides. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tsdf.h"
+
+namespace tsdf {
+
+constexpr int kSide = 8;                 // M: voxels per block axis
+constexpr int kBlockVoxels = 512;        // M^3
+constexpr int kTileWords = 4096;         // new-block bitmap words per scan tile
+constexpr int kTileThreads = 256;        // threads per scan tile (16 words each)
+constexpr unsigned kErrCapacity = 1u;    // sticky device error bits
+
+// Device-resident counters; every data-dependent size lives here so that a
+// sequence of calls needs no host round trip (and can be graph captured).
+struct Counters {
+    long long n_blocks;          // committed pool size
+    long long n_blocks_prev;     // pool size before the last allocation
+    unsigned int n_visible;      // entries in the integrate visible list
+    unsigned int n_visible_rc;   // entries in the raycast visible list
+    unsigned long long voxel_updates;
+    unsigned long long rays_hit;
+    unsigned int error;
+    unsigned int pad;
+    // totals over all calls before the current one (current = the fields above)
+    unsigned long long updates_total;
+    unsigned long long visible_total;
+    unsigned long long rays_total;
+    unsigned long long rc_blocks_total;
+};
+
+// One visible block for the integrate kernel: pool slot and the camera-space
+// position of its voxel (0,0,0), computed in double and carried as a float
+// hi/lo pair so that T_k = (D - z_hi) - (z_lo + dz) keeps full precision.
+struct __align__(16) VisibleBlock {
+    int slot;
+    float hi[3];
+    float lo[3];
+    int pad;
+};
+
+// Constants of one allocation call (rounded once from double on the host).
+struct AllocParams {
+    float M[9];          // R / s, row major
+    float a[3];          // (t - origin) / s
+    float dz;            // delta / J
+    float G;             // grid_dim as float
+    float fx, fy, cx, cy;
+    float depth_min, depth_max;
+    int J;
+    int nb;
+    int width, height;
+};
+
+// Constants of one integrate / raycast call.
+struct FrameParams {
+    double R[9];         // camera -> world rotation, row major
+    double t[3];         // camera centre in world
+    double origin[3];
+    double s;
+    float cs[9];         // cs[3 r + a] = s * R[a][r]: camera axis r per voxel step along world axis a
+    float Rs[9];         // R / s (world voxel units per camera unit)
+    float q0[3];         // (t - origin) / s
+    float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
+    float depth_min, depth_max;
+    float delta, Q, sigma_coeff;
+    float zlo, zhi;      // camera z range a block must reach to matter
+    float near_clip, far_clip;
+    int width, height;
+    int nb, G;
+};
+
+}  // namespace tsdf
+
+struct tsdf_volume {
+    tsdf_config cfg;
+    int device;
+    int num_sms;
+    int32_t nb;                    // blocks per axis
+    uint64_t n_table;              // nb^3 entries of the block table
+    uint32_t n_tiles;              // bitmap scan tiles
+    int32_t* blk_slot;             // [n_table] pool slot or -1 (the paper's offset buffer)
+    uint32_t* newbits;             // [n_tiles * kTileWords] new-block bitmap
+    uint32_t* tile_sums;           // [n_tiles]
+    int4* blocks;                  // [cap] bx, by, bz, allocation frame
+    float* T;                      // [cap * 512]
+    float* P;                      // [cap * 512]
+    tsdf::VisibleBlock* visible;   // [cap]
+    int* visible_rc;               // [cap]
+    tsdf::Counters* ctr;
+    unsigned int* range;           // raycast near / far maps, 2 * range_pixels
+    int64_t range_pixels;
+    int64_t frame;                 // host copy of the frame counter
+    cudaStream_t last_stream;
+    tsdf_status host_error;        // sticky CUDA error seen on the host
+};
+
+namespace tsdf {
+
+// Launchers (tsdf_alloc.cu, tsdf_integrate.cu, tsdf_raycast.cu).
+cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParams& p,
+                            int frame, cudaStream_t st);
+cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var,
+                             const FrameParams& p, cudaStream_t st);
+cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
+                           float* normal_out, float* vertex_out, cudaStream_t st);
+cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out,
+                                      cudaStream_t st);
+
+// Host-side constant preparation (tsdf_volume.cu).
+AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);
+FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);
+
+__device__ __forceinline__ bool depth_ok(float d, float dmin, float dmax) {
+    return isfinite(d) && d > 0.0f && d >= dmin && d <= dmax;
+}
+
+__device__ __forceinline__ unsigned int warp_sum(unsigned int x) {
+    return __reduce_add_sync(0xffffffffu, x);
+}
+
+}  // namespace tsdf

@@ -1,0 +1,354 @@
+// Volume lifecycle and the C ABI entry points of libtsdf (declared in tsdf.h).
+//
+// Device layout (section "Volumetric Scene Representation", Figs. 4-5: an N^3
+// offset buffer, -1 for empty blocks, and a pool of M^3-voxel blocks):
+//   blk_slot   int32 [(G/8)^3]        pool slot of each block, -1 = empty. At
+//                                     the largest grids used (4096^3 voxels) this
+//                                     is 512 MB: cheap on a 270 GB device, and a
+//                                     lookup is one load with no probing.
+//   blocks     int4  [capacity]       bx, by, bz, allocation frame per slot
+//   T, P       float [capacity * 512] distance and variance, structure of arrays
+//                                     so that raycasting streams T alone
+//   newbits    uint32 bitmap of blocks allocated by the current call
+//   visible    per-call visible block lists; Counters holds every
+//              data-dependent size on the device.
+// All per-call constants (inverse pose, scaled rotations) are prepared here on
+// the host in double precision and passed by value to the kernels.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "tsdf_internal.cuh"
+
+using tsdf::AllocParams;
+using tsdf::Counters;
+using tsdf::FrameParams;
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+bool pose_ok(const double* pose) {
+    if (!pose) return false;
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(pose[i])) return false;
+    return true;
+}
+
+bool intr_ok(const tsdf_intrinsics* K) {
+    if (!K) return false;
+    if (!(std::isfinite(K->fx) && std::isfinite(K->fy) && std::isfinite(K->cx) && std::isfinite(K->cy)))
+        return false;
+    if (K->fx == 0.0f || K->fy == 0.0f) return false;
+    if (K->width <= 0 || K->height <= 0) return false;
+    return (int64_t)K->width * (int64_t)K->height < (int64_t)1 << 31;
+}
+
+tsdf_status fail_cuda(tsdf_volume* v, cudaError_t e) {
+    if (e == cudaSuccess) return TSDF_OK;
+    if (v && v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;
+    return TSDF_ERR_CUDA;
+}
+
+void free_all(tsdf_volume* v) {
+    cudaFree(v->blk_slot);
+    cudaFree(v->newbits);
+    cudaFree(v->tile_sums);
+    cudaFree(v->blocks);
+    cudaFree(v->T);
+    cudaFree(v->P);
+    cudaFree(v->visible);
+    cudaFree(v->visible_rc);
+    cudaFree(v->ctr);
+    cudaFree(v->range);
+}
+
+}  // namespace
+
+namespace tsdf {
+
+AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose) {
+    AllocParams p;
+    const double s = (double)v->cfg.voxel_size;
+    const double delta = (double)v->cfg.truncation;
+    p.J = v->cfg.alloc_half_samples > 0 ? v->cfg.alloc_half_samples : (int)std::ceil(2.0 * delta / s - 1e-6);
+    p.dz = (float)(delta / (double)p.J);
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) p.M[3 * r + k] = (float)(pose[4 * r + k] / s);
+        p.a[r] = (float)((pose[4 * r + 3] - v->cfg.origin[r]) / s);
+    }
+    p.G = (float)v->cfg.grid_dim;
+    p.fx = K.fx; p.fy = K.fy; p.cx = K.cx; p.cy = K.cy;
+    p.depth_min = v->cfg.depth_min;
+    p.depth_max = v->cfg.depth_max;
+    p.nb = v->nb;
+    p.width = K.width;
+    p.height = K.height;
+    return p;
+}
+
+FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose) {
+    FrameParams p;
+    const double s = (double)v->cfg.voxel_size;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) p.R[3 * r + k] = pose[4 * r + k];
+        p.t[r] = pose[4 * r + 3];
+        p.origin[r] = v->cfg.origin[r];
+    }
+    p.s = s;
+    for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a) {
+            p.cs[3 * r + a] = (float)(s * p.R[3 * a + r]);
+            p.Rs[3 * r + a] = (float)(p.R[3 * r + a] / s);
+        }
+    for (int r = 0; r < 3; ++r) p.q0[r] = (float)((p.t[r] - p.origin[r]) / s);
+    p.fx = K.fx; p.fy = K.fy; p.cx = K.cx; p.cy = K.cy;
+    p.cxh = (float)((double)K.cx + 0.5);
+    p.cyh = (float)((double)K.cy + 0.5);
+    p.depth_min = v->cfg.depth_min;
+    p.depth_max = v->cfg.depth_max;
+    p.delta = v->cfg.truncation;
+    p.Q = v->cfg.process_variance;
+    p.sigma_coeff = v->cfg.sigma_coeff;
+    const double dl = 1.01 * (double)v->cfg.truncation;
+    p.zlo = (float)((double)v->cfg.depth_min - dl);
+    p.zhi = (float)((double)v->cfg.depth_max + dl);
+    p.near_clip = v->cfg.raycast_near;
+    p.far_clip = v->cfg.raycast_far;
+    p.width = K.width;
+    p.height = K.height;
+    p.nb = v->nb;
+    p.G = v->cfg.grid_dim;
+    return p;
+}
+
+}  // namespace tsdf
+
+extern "C" {
+
+void tsdf_config_default(tsdf_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->voxel_size = 1.5e-3f;
+    c->truncation = 7.5e-3f;
+    c->grid_dim = 2048;
+    for (int r = 0; r < 3; ++r) c->origin[r] = -0.5 * c->grid_dim * (double)c->voxel_size;
+    c->block_capacity = (int64_t)1 << 20;
+    c->process_variance = 0.0f;
+    c->depth_min = 0.1f;
+    c->depth_max = 4.0f;
+    c->raycast_near = 0.1f;
+    c->raycast_far = 4.0f;
+    c->sigma_coeff = 1.5e-3f;
+    c->storage = TSDF_STORAGE_F32;
+    c->alloc_half_samples = 0;
+}
+
+const char* tsdf_status_string(tsdf_status s) {
+    switch (s) {
+        case TSDF_OK: return "ok";
+        case TSDF_ERR_INVALID_ARG: return "invalid argument";
+        case TSDF_ERR_CAPACITY: return "block pool full: new blocks were dropped";
+        case TSDF_ERR_HASH_FULL: return "block table full";
+        case TSDF_ERR_CUDA: return "CUDA error";
+        case TSDF_ERR_NOT_READY: return "not ready";
+        case TSDF_ERR_OUT_OF_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
+    if (!cfg || !out) return TSDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    const tsdf_config& c = *cfg;
+    if (!finite_pos(c.voxel_size) || !finite_pos(c.truncation)) return TSDF_ERR_INVALID_ARG;
+    if (c.grid_dim <= 0 || c.grid_dim % tsdf::kSide != 0) return TSDF_ERR_INVALID_ARG;
+    const uint64_t nb = (uint64_t)(c.grid_dim / tsdf::kSide);
+    if (nb * nb * nb >= ((uint64_t)1 << 32)) return TSDF_ERR_INVALID_ARG;
+    if (c.block_capacity <= 0 || c.block_capacity > (int64_t)0x7fffffff) return TSDF_ERR_INVALID_ARG;
+    if (!(std::isfinite(c.process_variance) && c.process_variance >= 0.0f)) return TSDF_ERR_INVALID_ARG;
+    if (!(std::isfinite(c.sigma_coeff) && c.sigma_coeff >= 0.0f)) return TSDF_ERR_INVALID_ARG;
+    if (!(c.depth_min >= 0.0f && c.depth_max > c.depth_min && !std::isnan(c.depth_max)))
+        return TSDF_ERR_INVALID_ARG;
+    if (!(finite_pos(c.raycast_near) && c.raycast_far > c.raycast_near && std::isfinite(c.raycast_far)))
+        return TSDF_ERR_INVALID_ARG;
+    if (c.storage != TSDF_STORAGE_F32) return TSDF_ERR_INVALID_ARG;
+    if (c.alloc_half_samples < 0 || c.alloc_half_samples > 4096) return TSDF_ERR_INVALID_ARG;
+    for (int r = 0; r < 3; ++r)
+        if (!std::isfinite(c.origin[r])) return TSDF_ERR_INVALID_ARG;
+    if (c.alloc_half_samples == 0 && std::ceil(2.0 * c.truncation / c.voxel_size - 1e-6) > 4096.0)
+        return TSDF_ERR_INVALID_ARG;
+
+    tsdf_volume* v = (tsdf_volume*)std::calloc(1, sizeof(tsdf_volume));
+    if (!v) return TSDF_ERR_OUT_OF_MEMORY;
+    v->cfg = c;
+    v->nb = (int32_t)nb;
+    v->n_table = nb * nb * nb;
+    const uint64_t words = (v->n_table + 31) / 32;
+    v->n_tiles = (uint32_t)((words + tsdf::kTileWords - 1) / tsdf::kTileWords);
+    v->host_error = TSDF_OK;
+    cudaError_t e = cudaGetDevice(&v->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device);
+    if (e != cudaSuccess) {
+        std::free(v);
+        return TSDF_ERR_CUDA;
+    }
+    const size_t cap = (size_t)c.block_capacity;
+    bool ok = true;
+    ok = ok && cudaMalloc(&v->blk_slot, v->n_table * sizeof(int32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->newbits, (size_t)v->n_tiles * tsdf::kTileWords * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->tile_sums, (size_t)v->n_tiles * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->blocks, cap * sizeof(int4)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->T, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->P, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->visible, cap * sizeof(tsdf::VisibleBlock)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->visible_rc, cap * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->ctr, sizeof(Counters)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(v);
+        std::free(v);
+        return TSDF_ERR_OUT_OF_MEMORY;
+    }
+    e = cudaMemset(v->blk_slot, 0xff, v->n_table * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(v->newbits, 0, (size_t)v->n_tiles * tsdf::kTileWords * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(v->ctr, 0, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_all(v);
+        std::free(v);
+        return TSDF_ERR_CUDA;
+    }
+    *out = v;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_create(float voxel_size, float truncation, int64_t block_capacity, tsdf_volume** out) {
+    tsdf_config c;
+    tsdf_config_default(&c);
+    c.voxel_size = voxel_size;
+    c.truncation = truncation;
+    c.block_capacity = block_capacity;
+    if (finite_pos(voxel_size))
+        for (int r = 0; r < 3; ++r) c.origin[r] = -0.5 * c.grid_dim * (double)voxel_size;
+    return tsdf_create_ex(&c, out);
+}
+
+void tsdf_destroy(tsdf_volume* v) {
+    if (!v) return;
+    if (v->last_stream) cudaStreamSynchronize(v->last_stream);
+    cudaDeviceSynchronize();
+    free_all(v);
+    std::free(v);
+}
+
+tsdf_status tsdf_reset(tsdf_volume* v, void* stream) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(v->blk_slot, 0xff, v->n_table * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->ctr, 0, sizeof(Counters), st);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    v->frame = 0;
+    v->host_error = TSDF_OK;
+    v->last_stream = st;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_allocate(tsdf_volume* v, const float* depth, const tsdf_intrinsics* K, const double pose_wc[16],
+                          void* stream) {
+    if (!v || !depth || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
+    const AllocParams p = tsdf::make_alloc_params(v, *K, pose_wc);
+    cudaStream_t st = (cudaStream_t)stream;
+    v->last_stream = st;
+    return fail_cuda(v, tsdf::launch_allocate(v, depth, p, (int)v->frame, st));
+}
+
+tsdf_status tsdf_integrate(tsdf_volume* v, const float* depth, const float* variance, const tsdf_intrinsics* K,
+                           const double pose_wc[16], void* stream) {
+    if (!v || !depth || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
+    const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
+    cudaStream_t st = (cudaStream_t)stream;
+    v->last_stream = st;
+    const tsdf_status s = fail_cuda(v, tsdf::launch_integrate(v, depth, variance, p, st));
+    if (s == TSDF_OK) ++v->frame;
+    return s;
+}
+
+tsdf_status tsdf_raycast(tsdf_volume* v, const tsdf_intrinsics* K, const double pose_wc[16], float* depth_out,
+                         float* normal_out, float* vertex_out, void* stream) {
+    if (!v || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
+    const int64_t npix = (int64_t)K->width * K->height;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (npix > v->range_pixels) {
+        // grow the range maps (synchronising: done once per new image size)
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaFree(v->range);
+        v->range = nullptr;
+        v->range_pixels = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)npix * sizeof(unsigned int));
+        if (e != cudaSuccess) return fail_cuda(v, e);
+        v->range_pixels = npix;
+    }
+    const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
+    v->last_stream = st;
+    return fail_cuda(v, tsdf::launch_raycast(v, p, depth_out, normal_out, vertex_out, st));
+}
+
+tsdf_status tsdf_quadratic_variance(const float* depth, int64_t n, float sigma_coeff, float* var_out,
+                                    void* stream) {
+    if (n < 0 || (n > 0 && (!depth || !var_out)) || !(std::isfinite(sigma_coeff) && sigma_coeff >= 0.0f))
+        return TSDF_ERR_INVALID_ARG;
+    return tsdf::launch_quadratic_variance(depth, n, sigma_coeff, var_out, (cudaStream_t)stream) == cudaSuccess
+               ? TSDF_OK
+               : TSDF_ERR_CUDA;
+}
+
+tsdf_status tsdf_get_status(tsdf_volume* v) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(v->last_stream);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    if (v->host_error != TSDF_OK) return v->host_error;
+    unsigned int err = 0;
+    e = cudaMemcpy(&err, &v->ctr->error, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    if (err & tsdf::kErrCapacity) return TSDF_ERR_CAPACITY;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* out) {
+    if (!v || !out) return TSDF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(v->last_stream);
+    Counters c;
+    if (e == cudaSuccess) e = cudaMemcpy(&c, v->ctr, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    out->n_blocks = c.n_blocks;
+    out->new_blocks = c.n_blocks - c.n_blocks_prev;
+    out->visible_blocks = c.n_visible;
+    out->voxel_updates = (int64_t)c.voxel_updates;
+    out->raycast_blocks = c.n_visible_rc;
+    out->rays_hit = (int64_t)c.rays_hit;
+    out->frames = v->frame;
+    out->voxel_updates_total = (int64_t)(c.updates_total + c.voxel_updates);
+    out->visible_blocks_total = (int64_t)(c.visible_total + c.n_visible);
+    out->rays_hit_total = (int64_t)(c.rays_total + c.rays_hit);
+    out->raycast_blocks_total = (int64_t)(c.rc_blocks_total + c.n_visible_rc);
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_export(tsdf_volume* v, int32_t* coords_frame, float* T, float* P, int64_t capacity,
+                        int64_t* n_out) {
+    if (!v || !n_out || capacity < 0) return TSDF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(v->last_stream);
+    long long n = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n, &v->ctr->n_blocks, sizeof(n), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    *n_out = n;
+    const size_t m = (size_t)(n < capacity ? n : capacity);
+    if (m == 0) return TSDF_OK;
+    if (coords_frame) e = cudaMemcpy(coords_frame, v->blocks, m * sizeof(int4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && T) e = cudaMemcpy(T, v->T, m * tsdf::kBlockVoxels * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && P) e = cudaMemcpy(P, v->P, m * tsdf::kBlockVoxels * sizeof(float), cudaMemcpyDeviceToHost);
+    return fail_cuda(v, e);
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+"""Per-frame live fusion loop over the C ABI (section "Pipeline Overview": scene
+rendering, registration, fusion per acquired depth map; registration is outside
+this library, so each frame is fused at its given pose and the fused model is
+raycast at that pose for the next frame's alignment).
+
+``FusionPipeline.step`` enqueues allocate -> integrate -> raycast for one depth
+map already on the device; ``step_host`` first copies a pinned host depth map
+into one of two device staging buffers on the same stream. Nothing here
+synchronises: results are read by the caller when needed.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from . import tsdf
+
+
+class FusionPipeline:
+    def __init__(self, volume: tsdf.Volume, intr, device: Optional[torch.device] = None):
+        self.volume = volume
+        self.intr = intr
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        H, W = intr.height, intr.width
+        self.depth_map = torch.empty((H, W), dtype=torch.float32, device=dev)
+        self.normal_map = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        self.vertex_map = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        self._staging = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(2)]
+        self._k = 0
+
+    @property
+    def maps(self):
+        return self.depth_map, self.normal_map, self.vertex_map
+
+    def step(self, depth: torch.Tensor, pose, variance: Optional[torch.Tensor] = None, stream=None):
+        """Fuse one device depth map at ``pose`` and raycast the model at ``pose``."""
+        self.volume.allocate(depth, self.intr, pose, stream)
+        self.volume.integrate(depth, self.intr, pose, variance, stream)
+        self.volume.raycast(self.intr, pose, out=self.maps, stream=stream)
+
+    def step_host(self, depth_host: torch.Tensor, pose, stream=None):
+        """Copy a (pinned) host depth map to the device, then ``step``."""
+        buf = self._staging[self._k & 1]
+        self._k += 1
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            buf.copy_(depth_host, non_blocking=True)
+        self.step(buf, pose, stream=s)

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libtsdf.so (include/tsdf.h) for torch CUDA tensors.
+
+Argument marshalling only: every step of allocation, integration and raycasting
+runs in the library's CUDA kernels. There is no CPU fallback: if the library is
+missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtsdf.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_HASH_FULL, ERR_CUDA, ERR_NOT_READY, ERR_OUT_OF_MEMORY = range(7)
+STORAGE_F32 = 0
+
+# Every function the header declares (checked against include/tsdf.h by the tests).
+EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
+            "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_raycast", "tsdf_quadratic_variance",
+            "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_float), ("truncation", ctypes.c_float),
+                ("origin", ctypes.c_double * 3), ("grid_dim", ctypes.c_int32),
+                ("block_capacity", ctypes.c_int64), ("process_variance", ctypes.c_float),
+                ("depth_min", ctypes.c_float), ("depth_max", ctypes.c_float),
+                ("raycast_near", ctypes.c_float), ("raycast_far", ctypes.c_float),
+                ("sigma_coeff", ctypes.c_float), ("storage", ctypes.c_int32),
+                ("alloc_half_samples", ctypes.c_int32)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int64), ("new_blocks", ctypes.c_int64),
+                ("visible_blocks", ctypes.c_int64), ("voxel_updates", ctypes.c_int64),
+                ("raycast_blocks", ctypes.c_int64), ("rays_hit", ctypes.c_int64),
+                ("frames", ctypes.c_int64), ("voxel_updates_total", ctypes.c_int64),
+                ("visible_blocks_total", ctypes.c_int64), ("rays_hit_total", ctypes.c_int64),
+                ("raycast_blocks_total", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib: Optional[ctypes.CDLL] = None
+_P = ctypes.c_void_p
+_PD = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libtsdf.so (built by ``python -m paper_1311_7194_b300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libtsdf.so not found at {p}: build it with "
+                          "`python -m paper_1311_7194_b300.build` (needs nvcc)")
+    lib = ctypes.CDLL(p)
+    sig = {
+        "tsdf_config_default": (None, [ctypes.POINTER(Config)]),
+        "tsdf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "tsdf_create": (ctypes.c_int, [ctypes.c_float, ctypes.c_float, ctypes.c_int64, ctypes.POINTER(_P)]),
+        "tsdf_create_ex": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_P)]),
+        "tsdf_destroy": (None, [_P]),
+        "tsdf_reset": (ctypes.c_int, [_P, _P]),
+        "tsdf_allocate": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
+        "tsdf_integrate": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
+        "tsdf_raycast": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
+        "tsdf_quadratic_variance": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
+        "tsdf_get_status": (ctypes.c_int, [_P]),
+        "tsdf_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+        "tsdf_export": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().tsdf_status_string(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise TsdfError(status, what)
+
+
+def default_config() -> Config:
+    c = Config()
+    load().tsdf_config_default(ctypes.byref(c))
+    return c
+
+
+def config_from(vol, **overrides) -> Config:
+    """Config from a ``synth.VolumeParams``-like object (fields of the same names)."""
+    c = default_config()
+    c.voxel_size = vol.voxel_size
+    c.truncation = vol.truncation
+    c.origin = (ctypes.c_double * 3)(*[float(o) for o in vol.origin])
+    c.grid_dim = int(vol.grid_dim)
+    c.block_capacity = int(vol.block_capacity)
+    c.process_variance = getattr(vol, "process_variance", 0.0)
+    c.depth_min, c.depth_max = vol.depth_min, vol.depth_max
+    c.raycast_near, c.raycast_far = vol.raycast_near, vol.raycast_far
+    c.sigma_coeff = vol.sigma_coeff
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def intrinsics(intr) -> Intrinsics:
+    return Intrinsics(intr.fx, intr.fy, intr.cx, intr.cy, int(intr.width), int(intr.height))
+
+
+def _pose(pose) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(16))
+    return (ctypes.c_double * 16)(*a.tolist())
+
+
+def _dev_ptr(t, n: int, what: str) -> int:
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA torch tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{what} must be a contiguous float32 tensor of {n} elements")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+@dataclass
+class Export:
+    coords: np.ndarray       # (n, 3) int32 block coordinates, pool order
+    alloc_frame: np.ndarray  # (n,) int32
+    T: np.ndarray            # (n, 512) float32, NaN = chi
+    P: np.ndarray            # (n, 512) float32
+
+    def sorted(self, nb: int) -> "Export":
+        key = self.coords[:, 0].astype(np.int64) + nb * (self.coords[:, 1] + nb * self.coords[:, 2].astype(np.int64))
+        o = np.argsort(key, kind="stable")
+        return Export(self.coords[o], self.alloc_frame[o], self.T[o], self.P[o])
+
+
+class Volume:
+    """A sparse TSDF volume on the current CUDA device (tsdf_create_ex)."""
+
+    def __init__(self, config: Config):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtsdf needs a CUDA device")
+        self.lib = load()
+        self.config = config
+        h = _P()
+        _check(self.lib.tsdf_create_ex(ctypes.byref(config), ctypes.byref(h)), "tsdf_create_ex")
+        self.h = h
+
+    @classmethod
+    def from_params(cls, vol, **overrides) -> "Volume":
+        return cls(config_from(vol, **overrides))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsdf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nb(self) -> int:
+        return int(self.config.grid_dim) // 8
+
+    def reset(self, stream=None):
+        _check(self.lib.tsdf_reset(self.h, _stream(stream)), "tsdf_reset")
+
+    def allocate(self, depth, intr, pose, stream=None):
+        K = intrinsics(intr)
+        _check(self.lib.tsdf_allocate(self.h, _dev_ptr(depth, K.width * K.height, "depth"), ctypes.byref(K),
+                                      _pose(pose), _stream(stream)), "tsdf_allocate")
+
+    def integrate(self, depth, intr, pose, variance=None, stream=None):
+        K = intrinsics(intr)
+        n = K.width * K.height
+        _check(self.lib.tsdf_integrate(self.h, _dev_ptr(depth, n, "depth"), _dev_ptr(variance, n, "variance"),
+                                       ctypes.byref(K), _pose(pose), _stream(stream)), "tsdf_integrate")
+
+    def fuse(self, depth, intr, pose, variance=None, stream=None):
+        """Allocate then integrate one frame."""
+        self.allocate(depth, intr, pose, stream)
+        self.integrate(depth, intr, pose, variance, stream)
+
+    def raycast(self, intr, pose, out=None, stream=None):
+        """Returns (depth (H,W), normal (H,W,3), vertex (H,W,3)) CUDA tensors."""
+        import torch
+        K = intrinsics(intr)
+        H, W = K.height, K.width
+        if out is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = (torch.empty((H, W), dtype=torch.float32, device=dev),
+                   torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+                   torch.empty((H, W, 3), dtype=torch.float32, device=dev))
+        d, n, v = out
+        _check(self.lib.tsdf_raycast(self.h, ctypes.byref(K), _pose(pose), _dev_ptr(d, H * W, "depth_out"),
+                                     _dev_ptr(n, 3 * H * W, "normal_out"), _dev_ptr(v, 3 * H * W, "vertex_out"),
+                                     _stream(stream)), "tsdf_raycast")
+        return out
+
+    def status(self) -> int:
+        return int(self.lib.tsdf_get_status(self.h))
+
+    def check(self):
+        _check(self.status(), "tsdf_get_status")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.lib.tsdf_get_stats(self.h, ctypes.byref(s)), "tsdf_get_stats")
+        return s.as_dict()
+
+    def export(self, values: bool = True) -> Export:
+        n = ctypes.c_int64(0)
+        _check(self.lib.tsdf_export(self.h, None, None, None, 0, ctypes.byref(n)), "tsdf_export")
+        m = int(n.value)
+        cf = np.empty((m, 4), np.int32)
+        T = np.empty((m, 512), np.float32) if values else np.empty((m, 0), np.float32)
+        P = np.empty((m, 512), np.float32) if values else np.empty((m, 0), np.float32)
+        _check(self.lib.tsdf_export(self.h, cf.ctypes.data_as(_P), T.ctypes.data_as(_P) if values else None,
+                                    P.ctypes.data_as(_P) if values else None, m, ctypes.byref(n)), "tsdf_export")
+        return Export(cf[:, :3].copy(), cf[:, 3].copy(), T, P)
+
+
+def quadratic_variance(depth, sigma_coeff: float, out=None, stream=None):
+    import torch
+    n = depth.numel()
+    if out is None:
+        out = torch.empty_like(depth)
+    _check(load().tsdf_quadratic_variance(_dev_ptr(depth, n, "depth"), n, float(sigma_coeff),
+                                          _dev_ptr(out, n, "var_out"), _stream(stream)), "tsdf_quadratic_variance")
+    return out

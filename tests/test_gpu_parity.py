@@ -1,0 +1,222 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: block sets and allocation frames bit-exact; T within 1e-5 delta and P
+within 1e-5 relative with identical chi patterns on voxels the oracle does not
+flag as ambiguous; raycast hit/miss identical, depth within 0.1 voxel away from
+silhouettes.
+"""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_1311_7194_b300 import synth, tsdf
+
+pytestmark = pytest.mark.gpu
+
+AMB_PX = 5e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1311_7194_b300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _cuda(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def fuse_both(seq, vars_=None, check_each_frame=True, n_frames=None, **over):
+    vol = tsdf.Volume.from_params(seq.volume, **over)
+    seq = synth.with_volume(seq, **over)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, amb_px=AMB_PX)
+    nb = seq.volume.grid_dim // 8
+    n = seq.n_frames if n_frames is None else n_frames
+    for k in range(n):
+        var = None if vars_ is None else vars_[k]
+        vol.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k], _cuda(var))
+        ov.fuse(seq.depth[k], seq.poses[k], var)
+        if check_each_frame:
+            ge, oe = vol.export(values=False), ov.export(values=False)
+            r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
+            assert r["keys_equal"] and r["frames_equal"], (k, r)
+    return vol, ov, seq
+
+
+def check_values(vol, ov, seq):
+    nb = seq.volume.grid_dim // 8
+    ge, oe = vol.export(), ov.export()
+    r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
+    assert r["keys_equal"] and r["frames_equal"], r
+    _, _, gT, gP = compare.sort_by_key(ge.coords, ge.alloc_frame, ge.T, ge.P, nb)
+    v = compare.compare_values(gT, gP, oe.T, oe.P, oe.amb, seq.volume.truncation)
+    assert v["ok"], json.dumps(v)
+    assert v["ambiguous_valid_frac"] < 0.05, json.dumps(v)
+    return v
+
+
+def check_raycast(vol, ov, seq, pose, min_compared=100):
+    gd, gn, gv = (t.cpu().numpy() for t in vol.raycast(seq.intr, pose))
+    od, ovx, onr, ofl = ov.raycast(pose)
+    r = compare.compare_raycast(gd, gn, gv, od, ovx, onr, ofl, seq.intr, pose, seq.volume.voxel_size,
+                                seq.volume.truncation, field_fn=ov.field)
+    assert r["ok"], json.dumps(r)
+    assert r["compared"] >= min_compared, json.dumps(r)
+    return r
+
+
+def test_sphere_tiny_parity():
+    """160x120 sphere, 10 noisy frames, 256^3 grid of 1 mm voxels."""
+    seq = synth.sphere_sequence()
+    vol, ov, seq = fuse_both(seq)
+    vol.check()
+    v = check_values(vol, ov, seq)
+    assert v["compared"] > 200000
+    check_raycast(vol, ov, seq, seq.poses[-1], min_compared=1500)
+    check_raycast(vol, ov, seq, seq.poses[4], min_compared=1500)
+    st = vol.stats()
+    assert st["frames"] == seq.n_frames and st["n_blocks"] == ov.n_blocks
+
+
+def test_room_small_ragged_parity():
+    """Room scene at a ragged 157x117 size, 12 frames, 512^3 grid of 6 mm voxels:
+    many tiles, image sizes that are not multiples of the kernels' tiles."""
+    seq = synth.room_sequence(n_frames=12, width=157, height=117, grid_dim=512, voxel_size=6e-3,
+                              block_capacity=1 << 16)
+    vol, ov, seq = fuse_both(seq)
+    check_values(vol, ov, seq)
+    check_raycast(vol, ov, seq, seq.poses[-1], min_compared=3000)
+
+
+def test_variance_map_and_process_variance():
+    """Explicit per-pixel variance maps (the variance argument) and Q > 0."""
+    seq = synth.sphere_sequence(n_frames=6)
+    rng = np.random.default_rng(3)
+    vars_ = [rng.uniform(0.5e-7, 4e-7, seq.depth[0].shape).astype(np.float32) for _ in range(seq.n_frames)]
+    vol, ov, seq = fuse_both(seq, vars_=vars_, process_variance=2e-8)
+    check_values(vol, ov, seq)
+
+
+def test_quadratic_variance_helper():
+    d = np.random.default_rng(4).uniform(0.2, 4.0, 10007).astype(np.float32)
+    d[::97] = 0.0
+    d[5] = np.nan
+    out = tsdf.quadratic_variance(_cuda(d), 1.5e-3).cpu().numpy()
+    a = np.float32(1.5e-3)
+    ref = np.where(np.isfinite(d) & (d > 0), (a * d * d).astype(np.float32) ** 2, 0.0)
+    assert np.allclose(out, ref, rtol=1e-6, atol=0)
+
+
+def test_empty_and_invalid_depth():
+    """No valid measurement: nothing allocated, every ray misses."""
+    seq = synth.sphere_sequence(n_frames=2)
+    bad = np.zeros_like(seq.depth[0])
+    bad[::3] = -1.0
+    bad[1::3] = np.nan
+    bad[2::7] = np.inf
+    vol = tsdf.Volume.from_params(seq.volume)
+    vol.fuse(_cuda(bad), seq.intr, seq.poses[0])
+    assert vol.stats()["n_blocks"] == 0
+    d, n, v = vol.raycast(seq.intr, seq.poses[0])
+    assert (d == 0).all() and torch.isnan(v).all() and torch.isnan(n).all()
+    vol.check()
+
+
+def test_partially_invalid_depth_parity():
+    """NaN, Inf, negative and out-of-range pixels mixed into a real frame."""
+    seq = synth.sphere_sequence(n_frames=3)
+    rng = np.random.default_rng(5)
+    for k in range(seq.n_frames):
+        d = seq.depth[k]
+        m = rng.uniform(size=d.shape)
+        d[m < 0.05] = np.nan
+        d[(m >= 0.05) & (m < 0.1)] = np.inf
+        d[(m >= 0.1) & (m < 0.15)] = -0.3
+        d[(m >= 0.15) & (m < 0.2)] = 5.0
+    vol, ov, seq = fuse_both(seq)
+    check_values(vol, ov, seq)
+
+
+def test_capacity_overflow_keeps_lowest_keys():
+    seq = synth.sphere_sequence(n_frames=3)
+    vol, ov, seq = fuse_both(seq, block_capacity=700)
+    assert vol.status() == tsdf.ERR_CAPACITY
+    assert vol.stats()["n_blocks"] == 700 == ov.n_blocks
+    check_values(vol, ov, seq)
+
+
+def test_single_pixel_and_tiny_images():
+    for (W, H) in [(1, 1), (3, 2), (33, 1)]:
+        seq = synth.sphere_sequence(n_frames=2, width=W, height=H, f=140.0)
+        vol, ov, seq = fuse_both(seq)
+        check_values(vol, ov, seq)
+        gd, gn, gv = vol.raycast(seq.intr, seq.poses[-1])
+        assert gd.shape == (H, W)
+
+
+def test_reset_reproduces():
+    seq = synth.sphere_sequence(n_frames=3)
+    vol = tsdf.Volume.from_params(seq.volume)
+    outs = []
+    for _ in range(2):
+        vol.reset()
+        for k in range(seq.n_frames):
+            vol.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k])
+        e = vol.export()
+        outs.append(e)
+        assert vol.stats()["frames"] == seq.n_frames
+    assert np.array_equal(outs[0].coords, outs[1].coords)
+    assert np.array_equal(outs[0].T, outs[1].T, equal_nan=True)
+
+
+def test_room_fullsize_allocation_bit_exact():
+    """The bench workload's sizes (640x480, 2048^3 grid of 1.5 mm voxels): block
+    sets after each of the first frames equal the oracle's bit for bit."""
+    seq = synth.room_sequence(n_frames=6, device="cuda")
+    vol = tsdf.Volume.from_params(seq.volume)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, store_values=False)
+    nb = seq.volume.grid_dim // 8
+    for k in range(seq.n_frames):
+        vol.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k])
+        ov.allocate(seq.depth[k], seq.poses[k], k)
+        ge, oe = vol.export(values=False), ov.export(values=False)
+        r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
+        assert r["keys_equal"] and r["frames_equal"], (k, r)
+    assert ov.n_blocks > 50000
+
+
+def test_room_fullsize_sampled_voxels():
+    """Full-size room: sampled voxels' T and P after several frames, replayed one
+    by one by the oracle from their blocks' allocation frames."""
+    seq = synth.room_sequence(n_frames=8, device="cuda")
+    vol = tsdf.Volume.from_params(seq.volume)
+    for k in range(seq.n_frames):
+        vol.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k])
+    # allocation frames from the oracle's own allocation replay
+    ov = oracle.OracleVolume(seq.volume, seq.intr, store_values=False)
+    for k in range(seq.n_frames):
+        ov.allocate(seq.depth[k], seq.poses[k], k)
+    oe = ov.export(values=False)
+    rng = np.random.default_rng(9)
+    pick = rng.choice(oe.coords.shape[0], size=4000, replace=False)
+    local = rng.integers(0, 512, size=pick.size)
+    vox = oe.coords[pick] * 8 + np.stack([local & 7, (local >> 3) & 7, local >> 6], -1)
+    T, P, amb = oracle.replay_voxels(seq.volume, seq.intr, list(seq.depth), seq.poses, vox,
+                                     oe.alloc_frame[pick], amb_px=AMB_PX)
+    ge = vol.export()
+    nb = seq.volume.grid_dim // 8
+    keys = compare.block_keys(ge.coords, nb)
+    order = np.argsort(keys)
+    slot = order[np.searchsorted(keys[order], compare.block_keys(oe.coords[pick], nb))]
+    gT = ge.T[slot, local].astype(np.float64)
+    gP = ge.P[slot, local].astype(np.float64)
+    v = compare.compare_values(gT[:, None], gP[:, None], T[:, None], P[:, None], amb[:, None],
+                               seq.volume.truncation)
+    assert v["ok"], v
+    assert v["compared"] > 300, v
