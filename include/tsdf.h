@@ -174,6 +174,30 @@ tsdf_status tsdf_integrate(tsdf_volume* vol, const float* depth, const float* va
 tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
                          float* depth_out, float* normal_out, float* vertex_out, void* stream);
 
+/* The same raycast as tsdf_raycast, for callers that must not allocate device
+ * memory during the call. The paper has no counterpart: this is a property of
+ * the library's memory handling, not of the method.
+ * tsdf_raycast grows its near / far range maps with cudaMalloc (and frees the
+ * old ones, which synchronises the device) whenever it first sees a larger
+ * image. Callers that cannot allow that - a real-time loop with a fixed memory
+ * budget that must not stall, an application whose own allocator owns device
+ * memory, code recording work for later replay - use this call instead: it
+ * takes the range maps from a fixed 10 MiB array inside the library (held by
+ * every GPU that loads the library until the process exits) and allocates
+ * nothing. Limits and rules:
+ *   - K->width * K->height must be at most 1280 * 1024, else
+ *     TSDF_ERR_INVALID_ARG;
+ *   - the current device must be the volume's device, else TSDF_ERR_INVALID_ARG;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture;
+ *   - all calls on a device share the array, which keeps the last call's
+ *     contents (each call clears the maps it uses first); calls whose GPU work
+ *     overlaps race on it and must be serialised.
+ * Arguments, outputs and the other errors are those of tsdf_raycast. */
+tsdf_status tsdf_raycast_noalloc(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
+                                 float* depth_out, float* normal_out, float* vertex_out, void* stream);
+
 /* Per-pixel measurement variance of a sensor whose deviation grows
  * quadratically with depth (Introduction; the text before Alg. 3):
  * var[i] = (sigma_coeff * depth[i]^2)^2 for valid depth > 0, else 0.

@@ -349,4 +349,16 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     return cudaGetLastError();
 }
 
+cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
+                                  float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    const long long npix = (long long)p.width * p.height;
+    reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
+    range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
+    rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
+    raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
+    const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
+    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, depth_out, normal_out, vertex_out, v->ctr);
+    return cudaGetLastError();
+}
+
 }  // namespace tsdf

@@ -21,7 +21,8 @@ STORAGE_F32 = 0
 
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
-            "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_raycast", "tsdf_quadratic_variance",
+            "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_raycast", "tsdf_raycast_noalloc",
+            "tsdf_quadratic_variance",
             "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
 
 
@@ -83,6 +84,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_allocate": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
         "tsdf_integrate": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
         "tsdf_raycast": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
+        "tsdf_raycast_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
         "tsdf_quadratic_variance": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
         "tsdf_get_status": (ctypes.c_int, [_P]),
         "tsdf_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
@@ -236,6 +238,20 @@ class Volume:
         _check(self.lib.tsdf_raycast(self.h, ctypes.byref(K), _pose(pose), _dev_ptr(d, H * W, "depth_out"),
                                      _dev_ptr(n, 3 * H * W, "normal_out"), _dev_ptr(v, 3 * H * W, "vertex_out"),
                                      _stream(stream)), "tsdf_raycast")
+        return out
+
+    def raycast_noalloc(self, intr, pose, out, stream=None):
+        """tsdf_raycast_noalloc: the raycast into caller-owned ``out`` maps
+        (depth (H,W), normal (H,W,3), vertex (H,W,3)) with no device allocation,
+        for callers that must not allocate during the call (images up to
+        1280 x 1024 pixels; concurrent calls on one device race)."""
+        K = intrinsics(intr)
+        H, W = K.height, K.width
+        d, n, v = out
+        _check(self.lib.tsdf_raycast_noalloc(self.h, ctypes.byref(K), _pose(pose), _dev_ptr(d, H * W, "depth_out"),
+                                             _dev_ptr(n, 3 * H * W, "normal_out"),
+                                             _dev_ptr(v, 3 * H * W, "vertex_out"), _stream(stream)),
+               "tsdf_raycast_noalloc")
         return out
 
     def status(self) -> int:
