@@ -151,10 +151,12 @@ tsdf_status tsdf_allocate(tsdf_volume* vol, const float* depth, const tsdf_intri
  *   else:      P += Q; K = P/(P+p_k); T += K (T_k - T); P = (1-K) P
  *   then:      T = chi if |T| > delta.
  * p_k = variance[pixel] when variance != NULL (device, width*height float32),
- * else (sigma_coeff * D^2)^2. Only blocks whose box can reach the image and the
- * depth range are visited (a conservative cull); all other voxels are
- * unchanged. Increments the frame counter. Errors: TSDF_ERR_INVALID_ARG,
- * TSDF_ERR_CUDA. */
+ * else (sigma_coeff * D^2)^2. Only blocks whose box can reach the image, the
+ * depth range and the truncation band of the depth under their footprint are
+ * visited (a conservative cull: skipped voxels would all have T_k = chi); all
+ * other voxels are unchanged. The first call with an image larger than any
+ * before grows a small per-tile depth buffer (cudaMalloc, synchronising).
+ * Increments the frame counter. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
 tsdf_status tsdf_integrate(tsdf_volume* vol, const float* depth, const float* variance,
                            const tsdf_intrinsics* K, const double pose_wc[16], void* stream);
 

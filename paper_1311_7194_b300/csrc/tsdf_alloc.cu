@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
                                                                     const unsigned int* __restrict__ tile_sums,
                                                                     Counters* ctr, int* __restrict__ blk_slot,
                                                                     int4* __restrict__ blocks, long long cap,
-                                                                    int frame, int nb) {
+                                                                    int frame, int nb, unsigned int* __restrict__ occ2,
+                                                                    unsigned int* __restrict__ occ3, int n2, int n3) {
     __shared__ unsigned smem[32];
     __shared__ unsigned wsum[kTileThreads / 32];
     const int tile = blockIdx.x;
@@ -160,6 +161,11 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
                 const int bz = (int)(key / ((unsigned)nb * (unsigned)nb));
                 blk_slot[key] = (int)rank;
                 blocks[rank] = make_int4(bx, by, bz, frame);
+                // coarse occupancy used by the raycast to skip empty space
+                const unsigned c2 = (unsigned)(bx / kOcc2) + (unsigned)n2 * ((unsigned)(by / kOcc2) + (unsigned)n2 * (unsigned)(bz / kOcc2));
+                const unsigned c3 = (unsigned)(bx / kOcc3) + (unsigned)n3 * ((unsigned)(by / kOcc3) + (unsigned)n3 * (unsigned)(bz / kOcc3));
+                atomicOr(occ2 + (c2 >> 5), 1u << (c2 & 31u));
+                atomicOr(occ3 + (c3 >> 5), 1u << (c3 & 31u));
             } else {
                 over = true;
             }
@@ -212,7 +218,7 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
                                                             v->tile_sums);
     alloc_assign_kernel<<<v->n_tiles, kTileThreads, 0, st>>>(v->newbits, v->tile_sums, v->ctr,
                                                              v->blk_slot, v->blocks, v->cfg.block_capacity,
-                                                             frame, v->nb);
+                                                             frame, v->nb, v->occ2, v->occ3, v->n2, v->n3);
     alloc_finalize_kernel<<<1, 32, 0, st>>>(v->tile_sums, (int)v->n_tiles, v->ctr, v->cfg.block_capacity);
     init_blocks_kernel<<<v->num_sms * 4, 256, 0, st>>>(v->ctr, reinterpret_cast<float2*>(v->T),
                                                        reinterpret_cast<float2*>(v->P));

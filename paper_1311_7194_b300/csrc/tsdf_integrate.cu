@@ -1,9 +1,12 @@
 // Measurement integration (section "Integration of Measurements", Alg. 3).
 //
+//   depth_tiles:      per 8x8-pixel tile, the min and max valid measured depth.
 //   cull_kernel:      one thread per allocated block; keeps blocks whose box can
 //                     project into the image within the depth range where a
-//                     voxel can have |T_k| <= delta (a conservative superset of
-//                     dom(T_k), section "Updating Sparse Structure"), and stores
+//                     voxel can have |T_k| <= delta, and whose projected footprint
+//                     holds some depth within delta of the box's depth range (a
+//                     conservative superset of the blocks with T_k != chi,
+//                     dom(T_k) of section "Updating Sparse Structure"), and stores
 //                     the camera-space position of the block's first voxel,
 //                     computed in double and split into a float hi/lo pair.
 //   integrate_kernel: persistent CTAs of 128 threads walk the visible list; a
@@ -17,7 +20,12 @@
 // Precision: at 3 m a float's spacing (2.4e-7 m) exceeds 1e-5 of a 7.5 mm
 // truncation, so z is never formed as one float. T_k = (D - z_hi) - (z_lo + dz):
 // D - z_hi is exact (Sterbenz: both within a factor 2 whenever |T_k| <= delta),
-// z_lo + dz is small, and the result keeps full precision.
+// z_lo + dz is small, and the result keeps full precision. x and y only choose
+// the pixel and need no such care.
+//
+// A voxel whose camera z lies outside the block's reach of the band (the depth
+// range under the block's footprint widened by delta, from the cull) is
+// rejected before any projection: it cannot have |T_k| <= delta.
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -69,8 +77,71 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
            vmin <= (float)p.height - 0.5f + pad;
 }
 
+// Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
+// the tile has none. One warp per tile, two pixels per lane.
+__global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth, FrameParams p,
+                                                          float2* __restrict__ tiles) {
+    const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
+    const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles_x * tiles_y; t += warps) {
+        const int u = (t % tiles_x) * kDepthTile + (lane & 3) * 2;
+        const int v = (t / tiles_x) * kDepthTile + (lane >> 2);
+        float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+        if (v < p.height) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (u + k < p.width) {
+                    const float d = __ldg(depth + (size_t)v * p.width + u + k);
+                    if (depth_ok(d, p.depth_min, p.depth_max)) {
+                        lo = fminf(lo, d);
+                        hi = fmaxf(hi, d);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) tiles[t] = make_float2(lo, hi);
+    }
+}
+
+// Whether any pixel a voxel of the block can project to holds a depth within
+// delta of the block's camera-depth range: when none does, every voxel of the
+// block has T_k = chi and the block is skipped. rect: projected corners.
+__device__ __forceinline__ bool band_reachable(const FrameParams& p, const float2* __restrict__ tiles,
+                                               const float rect[4], float zmin, float zmax, float* dlo,
+                                               float* dhi) {
+    const float W = (float)p.width, H = (float)p.height;
+    // nearest-pixel indices the voxels can round to, widened by one pixel
+    const int u0 = max(0, (int)floorf(fminf(fmaxf(rect[0], -4.0f), W + 4.0f) + 0.5f) - 1);
+    const int u1 = min(p.width - 1, (int)floorf(fminf(fmaxf(rect[1], -4.0f), W + 4.0f) + 0.5f) + 1);
+    const int v0 = max(0, (int)floorf(fminf(fmaxf(rect[2], -4.0f), H + 4.0f) + 0.5f) - 1);
+    const int v1 = min(p.height - 1, (int)floorf(fminf(fmaxf(rect[3], -4.0f), H + 4.0f) + 0.5f) + 1);
+    if (u0 > u1 || v0 > v1) return false;
+    const int tx0 = u0 / kDepthTile, tx1 = u1 / kDepthTile, ty0 = v0 / kDepthTile, ty1 = v1 / kDepthTile;
+    if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) > 256) return true;   // very near blocks: no test
+    const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
+    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const float2 m = tiles[ty * tiles_x + tx];
+            lo = fminf(lo, m.x);
+            hi = fmaxf(hi, m.y);
+        }
+    const float slack = 1.01f * p.delta + 2e-6f * fabsf(zmax);
+    *dlo = lo - slack;
+    *dhi = hi + slack;
+    return lo <= zmax + slack && hi >= zmin - slack;
+}
+
 __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
-                                                   FrameParams p, VisibleBlock* __restrict__ vis) {
+                                                   FrameParams p, const float2* __restrict__ tiles,
+                                                   VisibleBlock* __restrict__ vis) {
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -78,11 +149,13 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
         const long long b = b0 + lane;
         bool keep = false;
         double o[3];
+        float zlo = -3.0e38f, zhi = 3.0e38f;
         if (b < n) {
             cam_block_origin(p, blocks[b], o);
             const float of[3] = {(float)o[0], (float)o[1], (float)o[2]};
             float zmin, zmax, rect[4];
             keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
+            if (keep && rect[0] > -1e29f) keep = band_reachable(p, tiles, rect, zmin, zmax, &zlo, &zhi);
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (!m) continue;
@@ -92,10 +165,10 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
         if (keep) {
             VisibleBlock e;
             e.slot = (int)b;
-            for (int r = 0; r < 3; ++r) {
-                e.hi[r] = (float)o[r];
-                e.lo[r] = (float)(o[r] - (double)e.hi[r]);
-            }
+            for (int r = 0; r < 3; ++r) e.o[r] = (float)o[r];
+            e.oz_lo = (float)(o[2] - (double)e.o[2]);
+            e.zlo = zlo;
+            e.zhi = zhi;
             e.pad = 0;
             vis[base + __popc(m & ((1u << lane) - 1u))] = e;
         }
@@ -103,21 +176,21 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
 }
 
 // Projective measurement T_k of one voxel (Fusion: project x onto the depth map,
-// distance to the measured point; chi when there is no measurement).
+// distance to the measured point; chi when there is no measurement). The voxel
+// is lx steps along the block's x rows from a row start whose camera position
+// is (xr, yr, o_z + zr); zr carries the low part of o_z.
 template <bool kVarMap>
-__device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float ly, float lz,
-                                        const float* __restrict__ depth, const float* __restrict__ var,
+__device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
+                                        float zr, const float* __restrict__ depth, const float* __restrict__ var,
                                         float* Tk, float* pk) {
-    const float dx = __fmaf_rn(lx, p.cs[0], __fmaf_rn(ly, p.cs[1], __fmul_rn(lz, p.cs[2])));
-    const float dy = __fmaf_rn(lx, p.cs[3], __fmaf_rn(ly, p.cs[4], __fmul_rn(lz, p.cs[5])));
-    const float dz = __fmaf_rn(lx, p.cs[6], __fmaf_rn(ly, p.cs[7], __fmul_rn(lz, p.cs[8])));
-    const float zs = __fadd_rn(vb.lo[2], dz);
-    const float z = __fadd_rn(vb.hi[2], zs);
-    if (!(z > 0.0f)) return false;
-    const float x = __fadd_rn(vb.hi[0], __fadd_rn(vb.lo[0], dx));
-    const float y = __fadd_rn(vb.hi[1], __fadd_rn(vb.lo[1], dy));
-    const float uf = __fmaf_rn(p.fx, __fdiv_rn(x, z), p.cxh);   // u + 1/2
-    const float vf = __fmaf_rn(p.fy, __fdiv_rn(y, z), p.cyh);
+    const float zs = __fmaf_rn(lx, p.cs[6], zr);
+    const float z = __fadd_rn(vb.o[2], zs);
+    if (!(z > 0.0f && z >= vb.zlo && z <= vb.zhi)) return false;   // out of reach of the band
+    const float x = __fmaf_rn(lx, p.cs[0], xr);
+    const float y = __fmaf_rn(lx, p.cs[3], yr);
+    const float rz = __frcp_rn(z);
+    const float uf = __fmaf_rn(p.fx, __fmul_rn(x, rz), p.cxh);   // u + 1/2
+    const float vf = __fmaf_rn(p.fy, __fmul_rn(y, rz), p.cyh);
     if (!(uf >= 0.0f && uf < (float)p.width && vf >= 0.0f && vf < (float)p.height)) return false;
     const int pix = (int)floorf(vf) * p.width + (int)floorf(uf);
     const float D = __ldg(depth + pix);
@@ -130,7 +203,7 @@ __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock
         pv = __fmul_rn(sg, sg);
     }
     if (!(pv > 0.0f && pv <= 3.0e38f)) return false;
-    const float t = __fsub_rn(__fsub_rn(D, vb.hi[2]), zs);
+    const float t = __fsub_rn(__fsub_rn(D, vb.o[2]), zs);
     if (!(fabsf(t) <= p.delta)) return false;
     *Tk = t;
     *pk = pv;
@@ -163,12 +236,16 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
     unsigned updates = 0;
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
         const VisibleBlock vb = vis[i];
+        // camera position of this thread's row start (lx = 0)
+        const float xr = __fmaf_rn(ly, p.cs[1], __fmaf_rn(lz, p.cs[2], vb.o[0]));
+        const float yr = __fmaf_rn(ly, p.cs[4], __fmaf_rn(lz, p.cs[5], vb.o[1]));
+        const float zr = __fmaf_rn(ly, p.cs[7], __fmaf_rn(lz, p.cs[8], vb.oz_lo));
         float tk[4], pk[4];
         bool ok[4];
         bool any = false;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, ly, lz, depth, var, &tk[e], &pk[e]);
+            ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
             any |= ok[e];
         }
         if (!any) continue;
@@ -202,7 +279,8 @@ __global__ void reset_frame_counters(Counters* ctr) {
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
                              cudaStream_t st) {
     reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
-    cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible);
+    depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(depth, p, v->dtiles);
+    cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)v->num_sms * 12;
     if (var)
         integrate_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);

@@ -14,6 +14,9 @@ constexpr int kBlockVoxels = 512;        // M^3
 constexpr int kTileWords = 4096;         // new-block bitmap words per scan tile
 constexpr int kTileThreads = 256;        // threads per scan tile (16 words each)
 constexpr unsigned kErrCapacity = 1u;    // sticky device error bits
+constexpr int kDepthTile = 8;            // depth min / max tiles used by the integrate cull
+constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
+constexpr int kOcc3 = 16;                // occupancy level 3: cells of 16^3 blocks (128 voxels a side)
 
 // Device-resident counters; every data-dependent size lives here so that a
 // sequence of calls needs no host round trip (and can be graph captured).
@@ -33,13 +36,17 @@ struct Counters {
     unsigned long long rc_blocks_total;
 };
 
-// One visible block for the integrate kernel: pool slot and the camera-space
-// position of its voxel (0,0,0), computed in double and carried as a float
-// hi/lo pair so that T_k = (D - z_hi) - (z_lo + dz) keeps full precision.
+// One visible block for the integrate kernel: pool slot, the camera-space
+// position of its voxel (0,0,0) computed in double and rounded to float (o),
+// the low part of its z (o[2] + oz_lo carries the double value, so that
+// T_k = (D - o_z) - (oz_lo + dz) keeps full precision), and the camera-z range
+// outside which no voxel of the block can lie within delta of a depth under its
+// footprint.
 struct __align__(16) VisibleBlock {
     int slot;
-    float hi[3];
-    float lo[3];
+    float o[3];
+    float oz_lo;
+    float zlo, zhi;
     int pad;
 };
 
@@ -65,6 +72,7 @@ struct FrameParams {
     float cs[9];         // cs[3 r + a] = s * R[a][r]: camera axis r per voxel step along world axis a
     float Rs[9];         // R / s (world voxel units per camera unit)
     float q0[3];         // (t - origin) / s
+    float oc0[3];        // camera position of voxel (0,0,0): R^T (origin - t)
     float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;
@@ -72,6 +80,7 @@ struct FrameParams {
     float near_clip, far_clip;
     int width, height;
     int nb, G;
+    int n2, n3;          // occupancy cells per axis at levels 2 and 3
 };
 
 }  // namespace tsdf
@@ -87,6 +96,10 @@ struct tsdf_volume {
     uint32_t* newbits;             // [n_tiles * kTileWords] new-block bitmap
     uint32_t* tile_sums;           // [n_tiles]
     int4* blocks;                  // [cap] bx, by, bz, allocation frame
+    uint32_t* occ2;                // bit per 4^3-block cell: holds an allocated block
+    uint32_t* occ3;                // bit per 16^3-block cell
+    int32_t n2, n3;                // cells per axis
+    size_t occ2_words, occ3_words;
     float* T;                      // [cap * 512]
     float* P;                      // [cap * 512]
     tsdf::VisibleBlock* visible;   // [cap]
@@ -94,6 +107,8 @@ struct tsdf_volume {
     tsdf::Counters* ctr;
     unsigned int* range;           // raycast near / far maps, 2 * range_pixels
     int64_t range_pixels;
+    float2* dtiles;                // per 8x8-pixel tile (min, max) of the valid depth
+    int64_t dtiles_cap;
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host

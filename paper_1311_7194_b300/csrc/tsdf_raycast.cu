@@ -7,19 +7,24 @@
 //   rc_cull_kernel:   allocated blocks whose box (widened by one voxel, the reach
 //                     of trilinear cells shared with neighbours) can project into
 //                     the image within [raycast_near, raycast_far].
-//   raster_kernel:    one warp per visible block: the block box's projected
-//                     bounding rectangle (dilated by a pixel) gets atomicMin of
-//                     the box's nearest camera z and atomicMax of its farthest,
-//                     on floats ordered as unsigned integers.
+//   raster_kernel:    one warp per visible block: every 4x4-pixel tile touched by
+//                     the block box's projected bounding rectangle (dilated by a
+//                     pixel) gets atomicMin of the box's nearest camera z and
+//                     atomicMax of its farthest, on floats ordered as unsigned
+//                     integers. Tiles rather than pixels cut the atomics 16-fold;
+//                     the range only bounds the march, so a looser one changes
+//                     which samples are taken, not which crossings exist.
 //   raycast_kernel:   one thread per pixel marches from near to far in camera z
 //                     with step delta/2 over the trilinear field of T; a sample
 //                     whose lower corner lies in an unallocated block jumps to
-//                     that block's exit. Where the field becomes defined already at
+//                     the exit of the largest empty cell around it (the block,
+//                     or a 4^3- or 16^3-block cell empty in the occupancy maps
+//                     kept by the allocation). Where the field becomes defined already at
 //                     or below zero, the last step is re-scanned in delta/32
 //                     substeps for a short positive run. At the first + to - pair
 //                     the crossing is
 //                     refined by Illinois false position (a secant method that keeps
-//                     a bracket) to 0.005 voxel, then
+//                     a bracket) to 0.02 voxel, then
 //                     the normal is the central difference of the field.
 // The coarse and fine stages run in one kernel: on sm_103a the register budget
 // that made the paper split them is not the limit, and fusing them avoids a
@@ -32,21 +37,20 @@ namespace {
 constexpr int kMaxMarch = 8192;     // bound on march iterations per ray
 constexpr int kRefine = 10;         // refinement samples per hit (Illinois false position)
 constexpr int kFine = 16;           // substeps of the re-scan on entering the field below zero
+constexpr int kRangeTile = 4;       // range maps hold one near / far pair per 4x4 pixels
 constexpr unsigned kFarInit = 0u;   // float bits of +0
 constexpr unsigned kNearInit = 0x7f800000u;   // float bits of +inf
 
-__device__ __forceinline__ void cam_point(const FrameParams& p, double X, double Y, double Z, float o[3]) {
-    const double x = X - p.t[0], y = Y - p.t[1], z = Z - p.t[2];
-    o[0] = (float)(p.R[0] * x + p.R[3] * y + p.R[6] * z);
-    o[1] = (float)(p.R[1] * x + p.R[4] * y + p.R[7] * z);
-    o[2] = (float)(p.R[2] * x + p.R[5] * y + p.R[8] * z);
-}
-
-// camera-space corners of the box spanning voxels [8b - 1, 8b + 8] of a block
+// camera-space corners of the box spanning voxels [8b - 1, 8b + 8] of a block,
+// in float from the camera position of voxel (0,0,0) (oc0) and the per-voxel
+// steps (cs): a few units of rounding at 3 m are far below the pixel of
+// dilation the raster adds.
 __device__ __forceinline__ void block_box(const FrameParams& p, int4 bc, float zr[2], float rect[4], bool* behind) {
+    const float bx = (float)(kSide * bc.x - 1), by = (float)(kSide * bc.y - 1), bz = (float)(kSide * bc.z - 1);
     float oc[3];
-    cam_point(p, p.origin[0] + (double)(kSide * bc.x - 1) * p.s, p.origin[1] + (double)(kSide * bc.y - 1) * p.s,
-              p.origin[2] + (double)(kSide * bc.z - 1) * p.s, oc);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        oc[r] = p.oc0[r] + bx * p.cs[3 * r] + by * p.cs[3 * r + 1] + bz * p.cs[3 * r + 2];
     const float ext = (float)(kSide + 1);
     float zmin = 3.0e38f, zmax = -3.0e38f, umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
 #pragma unroll
@@ -106,36 +110,65 @@ __global__ void __launch_bounds__(256) raster_kernel(const Counters* __restrict_
                                                      unsigned int* __restrict__ near_, unsigned int* __restrict__ far_) {
     const unsigned n = ctr->n_visible_rc;
     const int lane = threadIdx.x & 31;
-    const unsigned warps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += warps) {
-        float zr[2], rect[4];
-        bool behind;
-        block_box(p, blocks[vis[w]], zr, rect, &behind);
-        const float zn = fmaxf(zr[0], p.near_clip), zf = fminf(zr[1], p.far_clip);
-        if (!(zn <= zf)) continue;
-        int u0 = 0, u1 = p.width - 1, v0 = 0, v1 = p.height - 1;
-        if (!behind) {
-            u0 = max(u0, (int)floorf(fmaxf(rect[0], -2.0f)) - 1);
-            u1 = min(u1, (int)ceilf(fminf(rect[1], (float)p.width + 1.0f)) + 1);
-            v0 = max(v0, (int)floorf(fmaxf(rect[2], -2.0f)) - 1);
-            v1 = min(v1, (int)ceilf(fminf(rect[3], (float)p.height + 1.0f)) + 1);
+    const int tiles_x = (p.width + kRangeTile - 1) / kRangeTile;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < n; w0 += stride) {
+        // each lane bounds one block: tile rectangle and clipped depth range
+        int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
+        unsigned zn_bits = 0, zf_bits = 0;
+        if (w0 + lane < n) {
+            float zr[2], rect[4];
+            bool behind;
+            block_box(p, blocks[vis[w0 + lane]], zr, rect, &behind);
+            const float zn = fmaxf(zr[0], p.near_clip), zf = fminf(zr[1], p.far_clip);
+            if (zn <= zf) {
+                int u0 = 0, u1 = p.width - 1, v0 = 0, v1 = p.height - 1;
+                if (!behind) {
+                    u0 = max(u0, (int)floorf(fmaxf(rect[0], -2.0f)) - 1);
+                    u1 = min(u1, (int)ceilf(fminf(rect[1], (float)p.width + 1.0f)) + 1);
+                    v0 = max(v0, (int)floorf(fmaxf(rect[2], -2.0f)) - 1);
+                    v1 = min(v1, (int)ceilf(fminf(rect[3], (float)p.height + 1.0f)) + 1);
+                }
+                if (u0 <= u1 && v0 <= v1) {
+                    tx0 = u0 / kRangeTile; tx1 = u1 / kRangeTile;
+                    ty0 = v0 / kRangeTile; ty1 = v1 / kRangeTile;
+                    zn_bits = __float_as_uint(zn);
+                    zf_bits = __float_as_uint(zf);
+                }
+            }
         }
-        if (u0 > u1 || v0 > v1) continue;
-        const int cols = u1 - u0 + 1;
-        const int count = cols * (v1 - v0 + 1);
-        const unsigned zn_bits = __float_as_uint(zn), zf_bits = __float_as_uint(zf);
-        for (int k = lane; k < count; k += 32) {
-            const int pix = (v0 + k / cols) * p.width + u0 + k % cols;
-            atomicMin(near_ + pix, zn_bits);
-            atomicMax(far_ + pix, zf_bits);
+        // the warp writes the lanes' rectangles one after another
+        for (int j = 0; j < 32; ++j) {
+            const int a0 = __shfl_sync(0xffffffffu, tx0, j), a1 = __shfl_sync(0xffffffffu, tx1, j);
+            const int b0 = __shfl_sync(0xffffffffu, ty0, j), b1 = __shfl_sync(0xffffffffu, ty1, j);
+            const unsigned zn_j = __shfl_sync(0xffffffffu, zn_bits, j), zf_j = __shfl_sync(0xffffffffu, zf_bits, j);
+            if (a0 > a1 || b0 > b1) continue;
+            const int cols = a1 - a0 + 1;
+            const int count = cols * (b1 - b0 + 1);
+            for (int k = lane; k < count; k += 32) {
+                const int tile = (b0 + k / cols) * tiles_x + a0 + k % cols;
+                atomicMin(near_ + tile, zn_j);
+                atomicMax(far_ + tile, zf_j);
+            }
         }
     }
+}
+
+__device__ __forceinline__ int slot_of(const FrameParams& p, const int* __restrict__ table, int bx, int by, int bz) {
+    return __ldg(table + (unsigned)bx + (unsigned)p.nb * ((unsigned)by + (unsigned)p.nb * (unsigned)bz));
+}
+
+__device__ __forceinline__ float voxel(const float* __restrict__ T, int slot, int off) {
+    return slot < 0 ? __int_as_float(0x7fc00000) : __ldg(T + (size_t)slot * kBlockVoxels + off);
 }
 
 // Trilinear T at voxel-space point q. Returns 0 = defined (value in *f),
 // 1 = undefined (a corner is chi, unallocated or outside the grid),
 // 2 = the lower corner's block is unallocated or outside the grid (the caller
-// may skip the whole block).
+// may skip empty space; blk receives that block's coordinates).
+// The 8 corners are fetched by the same instructions whether or not the cell
+// crosses a block face (only the extra block lookups are conditional), which
+// keeps the lanes of a warp together.
 __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __restrict__ table,
                                          const float* __restrict__ T, float qx, float qy, float qz, float* f,
                                          int* blk) {
@@ -146,30 +179,33 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
     const int bx = ix >> 3, by = iy >> 3, bz = iz >> 3;
     blk[0] = bx; blk[1] = by; blk[2] = bz;
     if (bx < 0 || by < 0 || bz < 0 || bx >= p.nb || by >= p.nb || bz >= p.nb) return 2;
-    const int s0 = __ldg(table + (unsigned)bx + (unsigned)p.nb * ((unsigned)by + (unsigned)p.nb * (unsigned)bz));
-    if (s0 < 0) return 2;
+    const int s000 = slot_of(p, table, bx, by, bz);
+    if (s000 < 0) return 2;
     if (ix + 1 >= p.G || iy + 1 >= p.G || iz + 1 >= p.G) return 1;
-    const float tx = qx - fx0, ty = qy - fy0, tz = qz - fz0;
-    float c[8];
     const int lx = ix & 7, ly = iy & 7, lz = iz & 7;
-    if (lx < 7 && ly < 7 && lz < 7) {
-        const float* b = T + (size_t)s0 * kBlockVoxels + lx + 8 * ly + 64 * lz;
-        c[0] = __ldg(b); c[1] = __ldg(b + 1); c[2] = __ldg(b + 8); c[3] = __ldg(b + 9);
-        c[4] = __ldg(b + 64); c[5] = __ldg(b + 65); c[6] = __ldg(b + 72); c[7] = __ldg(b + 73);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int jx = ix + (k & 1), jy = iy + ((k >> 1) & 1), jz = iz + (k >> 2);
-            const int s = __ldg(table + (unsigned)(jx >> 3) +
-                                (unsigned)p.nb * ((unsigned)(jy >> 3) + (unsigned)p.nb * (unsigned)(jz >> 3)));
-            c[k] = s < 0 ? __int_as_float(0x7fc00000)
-                         : __ldg(T + (size_t)s * kBlockVoxels + (jx & 7) + 8 * (jy & 7) + 64 * (jz & 7));
-        }
+    const int ex = lx == 7, ey = ly == 7, ez = lz == 7;
+    int s100 = s000, s010 = s000, s110 = s000, s001 = s000, s101 = s000, s011 = s000, s111 = s000;
+    if (ex | ey | ez) {   // corners in up to 8 blocks
+        if (ex) s100 = slot_of(p, table, bx + 1, by, bz);
+        if (ey) s010 = slot_of(p, table, bx, by + 1, bz);
+        if (ex | ey) s110 = slot_of(p, table, bx + ex, by + ey, bz);
+        if (ez) s001 = slot_of(p, table, bx, by, bz + 1);
+        if (ex | ez) s101 = slot_of(p, table, bx + ex, by, bz + ez);
+        if (ey | ez) s011 = slot_of(p, table, bx, by + ey, bz + ez);
+        s111 = slot_of(p, table, bx + ex, by + ey, bz + ez);
     }
-    const float c00 = __fmaf_rn(tx, c[1] - c[0], c[0]);
-    const float c10 = __fmaf_rn(tx, c[3] - c[2], c[2]);
-    const float c01 = __fmaf_rn(tx, c[5] - c[4], c[4]);
-    const float c11 = __fmaf_rn(tx, c[7] - c[6], c[6]);
+    const int x0 = lx, x1 = ex ? 0 : lx + 1;
+    const int y0 = 8 * ly, y1 = ey ? 0 : 8 * (ly + 1);
+    const int z0 = 64 * lz, z1 = ez ? 0 : 64 * (lz + 1);
+    const float c000 = voxel(T, s000, x0 + y0 + z0), c100 = voxel(T, s100, x1 + y0 + z0);
+    const float c010 = voxel(T, s010, x0 + y1 + z0), c110 = voxel(T, s110, x1 + y1 + z0);
+    const float c001 = voxel(T, s001, x0 + y0 + z1), c101 = voxel(T, s101, x1 + y0 + z1);
+    const float c011 = voxel(T, s011, x0 + y1 + z1), c111 = voxel(T, s111, x1 + y1 + z1);
+    const float tx = qx - fx0, ty = qy - fy0, tz = qz - fz0;
+    const float c00 = __fmaf_rn(tx, c100 - c000, c000);
+    const float c10 = __fmaf_rn(tx, c110 - c010, c010);
+    const float c01 = __fmaf_rn(tx, c101 - c001, c001);
+    const float c11 = __fmaf_rn(tx, c111 - c011, c011);
     const float c0 = __fmaf_rn(ty, c10 - c00, c00);
     const float c1 = __fmaf_rn(ty, c11 - c01, c01);
     const float v = __fmaf_rn(tz, c1 - c0, c0);
@@ -177,9 +213,40 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
     return isnan(v) ? 1 : 0;   // chi (NaN) in any corner makes the sum NaN
 }
 
+__device__ __forceinline__ bool occupied(const unsigned int* __restrict__ occ, int n, int cx, int cy, int cz) {
+    const unsigned c = (unsigned)cx + (unsigned)n * ((unsigned)cy + (unsigned)n * (unsigned)cz);
+    return (__ldg(occ + (c >> 5)) >> (c & 31u)) & 1u;
+}
+
+// Camera z at which the ray leaves the empty cell around block blk: the largest
+// of (16 blocks)^3, (4 blocks)^3 or the block itself that holds no allocated
+// block (outside the grid counts as empty). inv: 1 / dq per axis (0 where the
+// ray does not move along that axis).
+__device__ __forceinline__ float empty_exit(const FrameParams& p, const unsigned int* __restrict__ occ2,
+                                            const unsigned int* __restrict__ occ3, const int blk[3],
+                                            const float inv[3]) {
+    const bool inside = blk[0] >= 0 && blk[1] >= 0 && blk[2] >= 0 && blk[0] < p.nb && blk[1] < p.nb && blk[2] < p.nb;
+    int shift = 0;   // log2 of blocks per cell side
+    if (!inside || !occupied(occ3, p.n3, blk[0] >> 4, blk[1] >> 4, blk[2] >> 4))
+        shift = 4;
+    else if (!occupied(occ2, p.n2, blk[0] >> 2, blk[1] >> 2, blk[2] >> 2))
+        shift = 2;
+    const float size = (float)(kSide << shift);
+    float ze = 3.0e38f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float lo = (float)((blk[r] >> shift) << shift) * (float)kSide;
+        if (inv[r] > 0.0f) ze = fminf(ze, (lo + size - p.q0[r]) * inv[r]);
+        if (inv[r] < 0.0f) ze = fminf(ze, (lo - p.q0[r]) * inv[r]);
+    }
+    return ze;
+}
+
 __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const unsigned int* __restrict__ near_,
                                                       const unsigned int* __restrict__ far_,
                                                       const int* __restrict__ table, const float* __restrict__ T,
+                                                      const unsigned int* __restrict__ occ2,
+                                                      const unsigned int* __restrict__ occ3,
                                                       float* __restrict__ depth_out, float* __restrict__ normal_out,
                                                       float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
     const int u = blockIdx.x * 16 + (threadIdx.x & 15);
@@ -190,44 +257,44 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
         const int pix = v * p.width + u;
         const float nanf_ = __int_as_float(0x7fc00000);
         float zs = 0.0f, n[3] = {nanf_, nanf_, nanf_}, vert[3] = {nanf_, nanf_, nanf_};
-        const float zn = __uint_as_float(near_[pix]), zf = __uint_as_float(far_[pix]);
+        const int tile = (v / kRangeTile) * ((p.width + kRangeTile - 1) / kRangeTile) + u / kRangeTile;
+        const float zn = __uint_as_float(near_[tile]), zf = __uint_as_float(far_[tile]);
         if (zn <= zf) {
             // ray in camera z: world point t + z R dc, in voxel units q0 + z dq
             const float dcx = ((float)u - p.cx) / p.fx, dcy = ((float)v - p.cy) / p.fy;
             const float dqx = p.Rs[0] * dcx + p.Rs[1] * dcy + p.Rs[2];
             const float dqy = p.Rs[3] * dcx + p.Rs[4] * dcy + p.Rs[5];
             const float dqz = p.Rs[6] * dcx + p.Rs[7] * dcy + p.Rs[8];
+            const float inv[3] = {dqx != 0.0f ? 1.0f / dqx : 0.0f, dqy != 0.0f ? 1.0f / dqy : 0.0f,
+                                  dqz != 0.0f ? 1.0f / dqz : 0.0f};
             const float h = 0.5f * p.delta;
             float z = fmaxf(zn, p.near_clip);
             const float zend = fminf(zf, p.far_clip);
             bool prev_def = false, found = false;
             float fprev = 0.0f, zprev = 0.0f, f = 0.0f;
+            float zprev_any = z, zstep = h;   // last sample taken and the step since
             int blk[3];
             for (int it = 0; it < kMaxMarch && z <= zend; ++it) {
                 const int st = trilinear(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
                                          __fmaf_rn(z, dqz, p.q0[2]), &f, blk);
                 if (st == 2) {
-                    // leave the lower corner's block: first z where q crosses its box
-                    float ze = 3.0e38f;
-                    if (dqx > 0.0f) ze = fminf(ze, ((float)(8 * blk[0] + 8) - p.q0[0]) / dqx);
-                    if (dqx < 0.0f) ze = fminf(ze, ((float)(8 * blk[0]) - p.q0[0]) / dqx);
-                    if (dqy > 0.0f) ze = fminf(ze, ((float)(8 * blk[1] + 8) - p.q0[1]) / dqy);
-                    if (dqy < 0.0f) ze = fminf(ze, ((float)(8 * blk[1]) - p.q0[1]) / dqy);
-                    if (dqz > 0.0f) ze = fminf(ze, ((float)(8 * blk[2] + 8) - p.q0[2]) / dqz);
-                    if (dqz < 0.0f) ze = fminf(ze, ((float)(8 * blk[2]) - p.q0[2]) / dqz);
-                    z = fmaxf(ze, z) + 1e-3f * h;
+                    // everything before the empty cell's exit is undefined
+                    zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
+                    z = zprev_any + 1e-3f * h;
+                    zstep = z - zprev_any;
                     prev_def = false;
                     continue;
                 }
                 const bool def = st == 0;
                 if (def && !prev_def && f <= 0.0f && it > 0) {
                     // The field starts here already at or below zero: its positive
-                    // side may be a run shorter than one coarse step (the samples
+                    // side may be a run shorter than the last step (the samples
                     // before were undefined). Re-scan the last step finely.
                     bool ldef = false, stop = false;
                     float fl = 0.0f, zl = 0.0f;
+                    const float back = fminf(zstep, z - zprev_any);
                     for (int j = 0; j <= kFine; ++j) {
-                        const float zq = j == kFine ? z : z - h + (float)j * (h / (float)kFine);
+                        const float zq = j == kFine ? z : z - back + (float)j * (back / (float)kFine);
                         float fq = f;
                         const int sq = j == kFine ? 0
                                                   : trilinear(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
@@ -260,7 +327,12 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                 prev_def = def;
                 fprev = f;
                 zprev = z;
-                z += h;
+                zprev_any = z;
+                // chi or partly unallocated cells: no crossing can be bracketed by
+                // this sample, so the march takes a double step (a positive run
+                // hidden in it is found by the re-scan above)
+                zstep = def ? h : 2.0f * h;
+                z += zstep;
             }
             if (found) {
                 // Illinois-modified regula falsi on the bracket [zprev, z]: the
@@ -268,7 +340,7 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                 // which avoids the one-sided stagnation of plain false position on
                 // the piecewise-cubic trilinear field.
                 float z1 = zprev, f1 = fprev, z2 = z, f2 = f;
-                const float eps = 0.005f * (float)p.s;
+                const float eps = 0.02f * (float)p.s;
                 int side = 0;
                 zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
                 for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
@@ -337,7 +409,8 @@ __global__ void reset_rc_counters(Counters* ctr) {
 
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out, float* normal_out,
                            float* vertex_out, cudaStream_t st) {
-    const long long npix = (long long)p.width * p.height;
+    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
+                           ((p.height + kRangeTile - 1) / kRangeTile);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_pixels;
     reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
@@ -345,19 +418,22 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
     raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
-    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, depth_out, normal_out, vertex_out, v->ctr);
+    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, v->occ2, v->occ3, depth_out, normal_out,
+                                         vertex_out, v->ctr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
-    const long long npix = (long long)p.width * p.height;
+    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
+                           ((p.height + kRangeTile - 1) / kRangeTile);
     reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
     range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
     rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
     raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
-    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, depth_out, normal_out, vertex_out, v->ctr);
+    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, v->occ2, v->occ3, depth_out, normal_out,
+                                         vertex_out, v->ctr);
     return cudaGetLastError();
 }
 

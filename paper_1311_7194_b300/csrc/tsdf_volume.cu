@@ -7,6 +7,8 @@
 //                                     is 512 MB: cheap on a 270 GB device, and a
 //                                     lookup is one load with no probing.
 //   blocks     int4  [capacity]       bx, by, bz, allocation frame per slot
+//   occ2, occ3 bitmaps of 4^3- and 16^3-block cells holding any allocated block
+//                                     (empty-space skipping in the raycast)
 //   T, P       float [capacity * 512] distance and variance, structure of arrays
 //                                     so that raycasting streams T alone
 //   newbits    uint32 bitmap of blocks allocated by the current call
@@ -53,6 +55,8 @@ tsdf_status fail_cuda(tsdf_volume* v, cudaError_t e) {
 void free_all(tsdf_volume* v) {
     cudaFree(v->blk_slot);
     cudaFree(v->newbits);
+    cudaFree(v->occ2);
+    cudaFree(v->occ3);
     cudaFree(v->tile_sums);
     cudaFree(v->blocks);
     cudaFree(v->T);
@@ -61,6 +65,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->visible_rc);
     cudaFree(v->ctr);
     cudaFree(v->range);
+    cudaFree(v->dtiles);
 }
 
 }  // namespace
@@ -102,6 +107,9 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
             p.Rs[3 * r + a] = (float)(p.R[3 * r + a] / s);
         }
     for (int r = 0; r < 3; ++r) p.q0[r] = (float)((p.t[r] - p.origin[r]) / s);
+    for (int r = 0; r < 3; ++r)
+        p.oc0[r] = (float)(p.R[r] * (p.origin[0] - p.t[0]) + p.R[3 + r] * (p.origin[1] - p.t[1]) +
+                           p.R[6 + r] * (p.origin[2] - p.t[2]));
     p.fx = K.fx; p.fy = K.fy; p.cx = K.cx; p.cy = K.cy;
     p.cxh = (float)((double)K.cx + 0.5);
     p.cyh = (float)((double)K.cy + 0.5);
@@ -119,6 +127,8 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.height = K.height;
     p.nb = v->nb;
     p.G = v->cfg.grid_dim;
+    p.n2 = v->n2;
+    p.n3 = v->n3;
     return p;
 }
 
@@ -186,6 +196,10 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     v->n_table = nb * nb * nb;
     const uint64_t words = (v->n_table + 31) / 32;
     v->n_tiles = (uint32_t)((words + tsdf::kTileWords - 1) / tsdf::kTileWords);
+    v->n2 = (int32_t)((nb + tsdf::kOcc2 - 1) / tsdf::kOcc2);
+    v->n3 = (int32_t)((nb + tsdf::kOcc3 - 1) / tsdf::kOcc3);
+    v->occ2_words = ((size_t)v->n2 * v->n2 * v->n2 + 31) / 32;
+    v->occ3_words = ((size_t)v->n3 * v->n3 * v->n3 + 31) / 32;
     v->host_error = TSDF_OK;
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device);
@@ -199,6 +213,8 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     ok = ok && cudaMalloc(&v->newbits, (size_t)v->n_tiles * tsdf::kTileWords * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->tile_sums, (size_t)v->n_tiles * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->blocks, cap * sizeof(int4)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->occ2, v->occ2_words * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->occ3, v->occ3_words * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->T, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->P, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->visible, cap * sizeof(tsdf::VisibleBlock)) == cudaSuccess;
@@ -213,6 +229,8 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     e = cudaMemset(v->blk_slot, 0xff, v->n_table * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(v->newbits, 0, (size_t)v->n_tiles * tsdf::kTileWords * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(v->ctr, 0, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaMemset(v->occ2, 0, v->occ2_words * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(v->occ3, 0, v->occ3_words * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_all(v);
@@ -247,6 +265,8 @@ tsdf_status tsdf_reset(tsdf_volume* v, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(v->blk_slot, 0xff, v->n_table * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->ctr, 0, sizeof(Counters), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->occ2, 0, v->occ2_words * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->occ3, 0, v->occ3_words * sizeof(uint32_t), st);
     if (e != cudaSuccess) return fail_cuda(v, e);
     v->frame = 0;
     v->host_error = TSDF_OK;
@@ -266,8 +286,20 @@ tsdf_status tsdf_allocate(tsdf_volume* v, const float* depth, const tsdf_intrins
 tsdf_status tsdf_integrate(tsdf_volume* v, const float* depth, const float* variance, const tsdf_intrinsics* K,
                            const double pose_wc[16], void* stream) {
     if (!v || !depth || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
-    const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ntiles = (int64_t)((K->width + tsdf::kDepthTile - 1) / tsdf::kDepthTile) *
+                           ((K->height + tsdf::kDepthTile - 1) / tsdf::kDepthTile);
+    if (ntiles > v->dtiles_cap) {
+        // grow the depth tile buffer (synchronising: done once per new image size)
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaFree(v->dtiles);
+        v->dtiles = nullptr;
+        v->dtiles_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
+        if (e != cudaSuccess) return fail_cuda(v, e);
+        v->dtiles_cap = ntiles;
+    }
+    const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     v->last_stream = st;
     const tsdf_status s = fail_cuda(v, tsdf::launch_integrate(v, depth, variance, p, st));
     if (s == TSDF_OK) ++v->frame;
