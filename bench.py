@@ -49,7 +49,12 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--block-capacity", type=int, default=1 << 20, help="pool size in blocks")
+    ap.add_argument("--block-capacity", type=int, default=None, help="pool size in blocks")
+    ap.add_argument("--mode", choices=["graph", "direct"], default="graph",
+                    help="graph: each step one CUDA graph launch; direct: one C-ABI call per stage")
+    ap.add_argument("--workload", choices=["room", "batched"], default="room",
+                    help="room: per-frame live fusion (2048^3, 1.5 mm); batched: 3000^3 grid of 1 mm voxels, "
+                         "1000 frames fused K=8 per graph launch, raycast per batch")
     ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
     ap.add_argument("--cpu-ray-stride", type=int, default=8, help="oracle sample: pixel stride per axis")
     return ap.parse_args()
@@ -142,9 +147,12 @@ def oracle_sample(seq, frames, stride, ov=None, start=0):
     return (t_fuse + t_ray) / frames, ov
 
 
-def make_sequence(n_frames, device, block_capacity=1 << 20):
+def make_sequence(n_frames, device, block_capacity=None, workload="room"):
     from paper_1311_7194_b300 import synth
-    return synth.room_sequence(seed=1, n_frames=n_frames, device=device, block_capacity=block_capacity)
+    if workload == "batched":
+        return synth.room_sequence(seed=1, n_frames=n_frames, device=device, grid_dim=3000, voxel_size=1e-3,
+                                   block_capacity=block_capacity or (1 << 21), origin=(0.0, -0.036, 0.0))
+    return synth.room_sequence(seed=1, n_frames=n_frames, device=device, block_capacity=block_capacity or (1 << 20))
 
 
 def run_reference(args):
@@ -220,13 +228,16 @@ def run_ours(args):
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume)
-    pipe = FusionPipeline(vol, seq.intr, dev)
+    pipe = FusionPipeline(vol, seq.intr, dev, graph=args.mode == "graph")
     stream = torch.cuda.current_stream()
 
     def step(stage_events=None):
         vol.reset()
         for k in range(F):
             if stage_events is None:
+                pipe.step(depth_dev[k], seq.poses[k])
+            elif pipe.graph is not None:
+                pipe.graph.set_events(stage_events[k])     # recorded as nodes of the step's graph
                 pipe.step(depth_dev[k], seq.poses[k])
             else:
                 e = stage_events[k]
@@ -237,6 +248,8 @@ def run_ours(args):
                 e[2].record(stream)
                 vol.raycast(seq.intr, seq.poses[k], out=pipe.maps)
                 e[3].record(stream)
+        if pipe.graph is not None:
+            pipe.graph.set_events(None)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -310,7 +323,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: seeded analytic room scene, quadratic depth noise, edge dropout",
             "config": {"workload": WORKLOAD, "frames_per_step": F, "width": W, "height": H, "grid_dim": 2048,
-                       "voxel_size_m": 1.5e-3, "block_capacity": args.block_capacity, "parallelism": f"replicas x{world}",
+                       "voxel_size_m": 1.5e-3, "block_capacity": int(seq.volume.block_capacity),
+                       "launch": "one CUDA graph per frame" if args.mode == "graph" else "one C-ABI call per stage",
+                       "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step"},
             "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,
             "rays_per_s": rays_per_step * args.steps * world / elapsed_max,
@@ -366,10 +381,68 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched + graphed workload: 3000^3 grid of 1 mm voxels, 640x480,
+    frames fused K = 8 per graph launch (tsdf_integrate_batch semantics) with a
+    raycast at each batch's last pose."""
+    import numpy as np
+    import torch
+
+    from paper_1311_7194_b300 import build as pkg_build
+    from paper_1311_7194_b300 import tsdf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pkg_build.build()
+    K = 8
+    n = (args.frames if args.frames != 300 else 1000) // K * K
+    seq = make_sequence(n, dev, args.block_capacity, workload="batched")
+    F, H, W = seq.depth.shape
+    depth_dev = torch.from_numpy(seq.depth).to(dev)
+    vol = tsdf.Volume.from_params(seq.volume)
+    g = tsdf.Graph(vol, seq.intr, K)
+    maps = (torch.empty((H, W), device=dev), torch.empty((H, W, 3), device=dev), torch.empty((H, W, 3), device=dev))
+
+    def step():
+        vol.reset()
+        for k in range(0, F, K):
+            g.launch([depth_dev[k + j] for j in range(K)], seq.poses[k:k + K], maps)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    vol.check()
+    clocks = ClockSampler(0)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = t0.elapsed_time(t1) / 1000.0
+    st = vol.stats()
+    vol.check()
+    line = {"metric": METRIC, "value": F * args.steps / sec, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched + graphed: 640x480, 3000^3 grid of 1 mm voxels, {F} frames, K={K} per "
+                                   "graph launch, raycast per batch", "frames_per_step": F},
+            "voxel_updates_per_s": st["voxel_updates_total"] * args.steps / sec,
+            "rays_per_s": (F // K) * H * W * args.steps / sec,
+            "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "blocks": int(st["n_blocks"])},
+            "graph_instantiations": g.instantiations, "clocks": clk}
+    g.close()
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -160,6 +160,23 @@ tsdf_status tsdf_allocate(tsdf_volume* vol, const float* depth, const tsdf_intri
 tsdf_status tsdf_integrate(tsdf_volume* vol, const float* depth, const float* variance,
                            const tsdf_intrinsics* K, const double pose_wc[16], void* stream);
 
+/* Fuse K posed depth maps (1 <= K <= 8) in one pass: the same result, bit for
+ * bit, as K calls of tsdf_allocate followed by tsdf_integrate in order (frames
+ * numbered from the current frame counter). Each frame is allocated in turn
+ * (a block remembers the first frame that allocated it), then one kernel walks
+ * the union of the K frames' visible blocks, loads each voxel's T and P once,
+ * applies Alg. 3 for frames 0..K-1 in order - skipping frames before its
+ * block's allocation - and stores them once. depth: host array of K device
+ * pointers (width*height float32 each); variance: NULL (quadratic model for all
+ * frames) or a host array of K device pointers; K: shared intrinsics;
+ * poses_wc: host, K*16 doubles. The first call (and the first with a larger
+ * image) allocates batch buffers of 256 bytes per pool block (cudaMalloc,
+ * synchronising). Increments the frame counter by K. Errors:
+ * TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA; pool exhaustion as tsdf_allocate. */
+tsdf_status tsdf_integrate_batch(tsdf_volume* vol, int32_t K, const float* const* depth,
+                                 const float* const* variance, const tsdf_intrinsics* Kin,
+                                 const double* poses_wc, void* stream);
+
 /* Raycast the fused surface into depth / normal / vertex maps of size
  * K->width x K->height (section "Scene Rendering"). Per pixel, a range map made
  * by rasterising the boxes of the allocated blocks (nearest front / farthest
@@ -199,6 +216,33 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const doubl
  * Arguments, outputs and the other errors are those of tsdf_raycast. */
 tsdf_status tsdf_raycast_noalloc(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
                                  float* depth_out, float* normal_out, float* vertex_out, void* stream);
+
+/* CUDA-graph driver of the per-step pipeline (no counterpart in the paper; it
+ * removes per-kernel launch gaps). A step fuses K frames (1 <= K <= 8) exactly
+ * as tsdf_integrate (K = 1) or tsdf_integrate_batch (K > 1) would, then
+ * raycasts the model at the last frame's pose exactly as tsdf_raycast. The step
+ * is recorded by stream capture on a private stream and run as one graph
+ * launch; later steps update the same executable graph in place.
+ * tsdf_graph_create sizes every buffer the step needs for images of K->width x
+ * K->height (it may allocate and synchronise); tsdf_graph_launch then
+ * allocates nothing. One graph per volume at a time; calls on the graph and
+ * its volume must be serialised. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA,
+ * TSDF_ERR_OUT_OF_MEMORY (create). */
+typedef struct tsdf_graph tsdf_graph;
+tsdf_status tsdf_graph_create(tsdf_volume* vol, int32_t K, const tsdf_intrinsics* Kin, tsdf_graph** out);
+/* depth: host array of K device pointers; variance: NULL or K device pointers;
+ * poses_wc: host, K*16 doubles; outputs as tsdf_raycast (each may be NULL). */
+tsdf_status tsdf_graph_launch(tsdf_graph* g, const float* const* depth, const float* const* variance,
+                              const double* poses_wc, float* depth_out, float* normal_out,
+                              float* vertex_out, void* stream);
+/* Number of graph instantiations so far (1 after the first step when every
+ * update succeeded); -1 for NULL. */
+int64_t tsdf_graph_instantiations(const tsdf_graph* g);
+/* Events (cudaEvent_t as void*, created by the caller) recorded by the next
+ * launches before allocation, before integration, before the raycast and at
+ * the end of the step; NULL (or NULL entries) records none. */
+tsdf_status tsdf_graph_set_events(tsdf_graph* g, void* const events[4]);
+void tsdf_graph_destroy(tsdf_graph* g);
 
 /* Per-pixel measurement variance of a sensor whose deviation grows
  * quadratically with depth (Introduction; the text before Alg. 3):

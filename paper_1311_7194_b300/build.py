@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsdf.so")
-SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu"]
+SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu", "tsdf_graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # No FMA contraction: every fused multiply-add is written out (__fmaf_rn), so the
 # allocation arithmetic and the Kalman update are the same op sequence wherever

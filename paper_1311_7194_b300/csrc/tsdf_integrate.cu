@@ -139,6 +139,26 @@ __device__ __forceinline__ bool band_reachable(const FrameParams& p, const float
     return lo <= zmax + slack && hi >= zmin - slack;
 }
 
+// The visible-list entry of block b for one frame; false when no voxel of the
+// block can have T_k != chi in that frame.
+__device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* __restrict__ tiles, int4 bc, int slot,
+                                           VisibleBlock* e) {
+    double o[3];
+    cam_block_origin(p, bc, o);
+    const float of[3] = {(float)o[0], (float)o[1], (float)o[2]};
+    float zmin, zmax, rect[4];
+    float zlo = -3.0e38f, zhi = 3.0e38f;
+    bool keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
+    if (keep && rect[0] > -1e29f) keep = band_reachable(p, tiles, rect, zmin, zmax, &zlo, &zhi);
+    e->slot = slot;
+    for (int r = 0; r < 3; ++r) e->o[r] = of[r];
+    e->oz_lo = (float)(o[2] - (double)of[2]);
+    e->zlo = keep ? zlo : 3.0e38f;     // an empty range makes every voxel chi
+    e->zhi = keep ? zhi : -3.0e38f;
+    e->pad = 0;
+    return keep;
+}
+
 __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                    FrameParams p, const float2* __restrict__ tiles,
                                                    VisibleBlock* __restrict__ vis) {
@@ -147,15 +167,36 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
         const long long b = b0 + lane;
+        VisibleBlock e;
+        const bool keep = b < n && make_entry(p, tiles, blocks[b], (int)b, &e);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = e;
+    }
+}
+
+// Batched cull: a block joins the list when it is visible in any of the K
+// frames; its K entries (one per frame, empty for frames it cannot reach) are
+// stored together.
+__global__ void __launch_bounds__(256) cull_batch_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
+                                                         BatchParams bp, const float2* __restrict__ tiles,
+                                                         long long tiles_stride, VisibleBlock* __restrict__ vis) {
+    const long long n = ctr->n_blocks;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
+        const long long b = b0 + lane;
         bool keep = false;
-        double o[3];
-        float zlo = -3.0e38f, zhi = 3.0e38f;
+        int4 bc = make_int4(0, 0, 0, 0);
         if (b < n) {
-            cam_block_origin(p, blocks[b], o);
-            const float of[3] = {(float)o[0], (float)o[1], (float)o[2]};
-            float zmin, zmax, rect[4];
-            keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
-            if (keep && rect[0] > -1e29f) keep = band_reachable(p, tiles, rect, zmin, zmax, &zlo, &zhi);
+            bc = blocks[b];
+            for (int k = 0; k < bp.K; ++k) {
+                VisibleBlock e;
+                keep |= bp.f0 + k >= bc.w && make_entry(bp.fp[k], tiles + k * tiles_stride, bc, (int)b, &e);
+            }
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (!m) continue;
@@ -163,14 +204,12 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
         if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
         if (keep) {
-            VisibleBlock e;
-            e.slot = (int)b;
-            for (int r = 0; r < 3; ++r) e.o[r] = (float)o[r];
-            e.oz_lo = (float)(o[2] - (double)e.o[2]);
-            e.zlo = zlo;
-            e.zhi = zhi;
-            e.pad = 0;
-            vis[base + __popc(m & ((1u << lane) - 1u))] = e;
+            const size_t i = (size_t)(base + __popc(m & ((1u << lane) - 1u)));
+            for (int k = 0; k < bp.K; ++k) {
+                VisibleBlock e;
+                make_entry(bp.fp[k], tiles + k * tiles_stride, bc, (int)b, &e);
+                vis[i * kMaxBatch + k] = e;
+            }
         }
     }
 }
@@ -267,6 +306,67 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
     if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
 }
 
+// K frames in one pass: T and P of a voxel are loaded once (at its first valid
+// measurement), updated by Alg. 3 for frames 0..K-1 in order - skipping frames
+// before the block's allocation - and stored once. Same measurement and update
+// functions as integrate_kernel, so the result equals K sequential calls bit
+// for bit.
+template <bool kVarMap>
+__global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
+                                                                            const VisibleBlock* __restrict__ vis,
+                                                                            const int4* __restrict__ blocks,
+                                                                            float* __restrict__ T,
+                                                                            float* __restrict__ P, BatchParams bp) {
+    const unsigned nvis = ctr->n_visible;
+    const int v0 = threadIdx.x * 4;
+    const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
+    unsigned updates = 0;
+    for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
+        const VisibleBlock* ve = vis + (size_t)i * kMaxBatch;
+        const int slot = ve[0].slot;
+        const int first = blocks[slot].w - bp.f0;     // first batch frame that sees the block
+        const size_t off = (size_t)slot * kBlockVoxels + (size_t)v0;
+        float tv[4], pv[4];
+        bool loaded = false;
+        for (int k = max(first, 0); k < bp.K; ++k) {
+            const FrameParams& p = bp.fp[k];
+            const VisibleBlock vb = ve[k];
+            const float xr = __fmaf_rn(ly, p.cs[1], __fmaf_rn(lz, p.cs[2], vb.o[0]));
+            const float yr = __fmaf_rn(ly, p.cs[4], __fmaf_rn(lz, p.cs[5], vb.o[1]));
+            const float zr = __fmaf_rn(ly, p.cs[7], __fmaf_rn(lz, p.cs[8], vb.oz_lo));
+            float tk[4], pk[4];
+            bool ok[4];
+            bool any = false;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, xr, yr, zr, bp.depth[k], bp.var[k], &tk[e], &pk[e]);
+                any |= ok[e];
+            }
+            if (!any) continue;
+            if (!loaded) {
+                const float4 t4 = *reinterpret_cast<const float4*>(T + off);
+                const float4 p4 = *reinterpret_cast<const float4*>(P + off);
+                tv[0] = t4.x; tv[1] = t4.y; tv[2] = t4.z; tv[3] = t4.w;
+                pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+                loaded = true;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (ok[e]) {
+                    kalman(tv[e], pv[e], tk[e], pk[e], p.Q, p.delta);
+                    ++updates;
+                }
+            }
+        }
+        if (loaded) {
+            *reinterpret_cast<float4*>(T + off) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        }
+    }
+    updates = warp_sum(updates);
+    if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+}
+
 __global__ void reset_frame_counters(Counters* ctr) {
     ctr->updates_total += ctr->voxel_updates;
     ctr->visible_total += ctr->n_visible;
@@ -286,6 +386,23 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
         integrate_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
     else
         integrate_kernel<false><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st) {
+    reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
+    for (int k = 0; k < bp.K; ++k)
+        depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(bp.depth[k], bp.fp[k],
+                                                            v->dtiles_batch + k * v->dtiles_batch_stride);
+    cull_batch_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, bp, v->dtiles_batch,
+                                                      v->dtiles_batch_stride, v->visible_batch);
+    const unsigned grid = (unsigned)v->num_sms * 12;
+    if (bp.var[0])
+        integrate_batch_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, v->T,
+                                                                         v->P, bp);
+    else
+        integrate_batch_kernel<false><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, v->T,
+                                                                          v->P, bp);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ constexpr int kTileWords = 4096;         // new-block bitmap words per scan tile
 constexpr int kTileThreads = 256;        // threads per scan tile (16 words each)
 constexpr unsigned kErrCapacity = 1u;    // sticky device error bits
 constexpr int kDepthTile = 8;            // depth min / max tiles used by the integrate cull
+constexpr int kMaxBatch = 8;             // frames per tsdf_integrate_batch call
 constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
 constexpr int kOcc3 = 16;                // occupancy level 3: cells of 16^3 blocks (128 voxels a side)
 
@@ -83,6 +84,15 @@ struct FrameParams {
     int n2, n3;          // occupancy cells per axis at levels 2 and 3
 };
 
+// Constants of one batched integrate call: K frames fused in order.
+struct BatchParams {
+    FrameParams fp[kMaxBatch];
+    const float* depth[kMaxBatch];
+    const float* var[kMaxBatch];
+    int K;
+    int f0;              // frame counter of the batch's first frame
+};
+
 }  // namespace tsdf
 
 struct tsdf_volume {
@@ -109,6 +119,9 @@ struct tsdf_volume {
     int64_t range_pixels;
     float2* dtiles;                // per 8x8-pixel tile (min, max) of the valid depth
     int64_t dtiles_cap;
+    tsdf::VisibleBlock* visible_batch;   // [cap * kMaxBatch] per (block, frame) entries of a batch
+    float2* dtiles_batch;          // [kMaxBatch * dtiles_batch_stride]
+    int64_t dtiles_batch_stride;
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host
@@ -121,6 +134,7 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
                             int frame, cudaStream_t st);
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var,
                              const FrameParams& p, cudaStream_t st);
+cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st);
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
 // Raycast with caller-provided near / far range maps (each W*H words).
@@ -128,6 +142,13 @@ cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st);
 cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out,
                                       cudaStream_t st);
+
+// Lazily grown per-image buffers and argument checks (tsdf_volume.cu).
+cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st);
+cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st);
+cudaError_t ensure_range(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st);
+bool pose_valid(const double* pose);
+bool intrinsics_valid(const tsdf_intrinsics* K);
 
 // Host-side constant preparation (tsdf_volume.cu).
 AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);

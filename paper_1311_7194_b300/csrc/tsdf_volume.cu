@@ -66,6 +66,8 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->ctr);
     cudaFree(v->range);
     cudaFree(v->dtiles);
+    cudaFree(v->visible_batch);
+    cudaFree(v->dtiles_batch);
 }
 
 }  // namespace
@@ -131,6 +133,53 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.n3 = v->n3;
     return p;
 }
+
+// Lazily grown per-image buffers. Each growth synchronises the stream (and
+// frees the old buffer), so it happens only on the first call with a larger
+// image; tsdf_graph_create calls them up front so that nothing allocates
+// during stream capture.
+cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
+    const int64_t ntiles = (int64_t)((K.width + kDepthTile - 1) / kDepthTile) * ((K.height + kDepthTile - 1) / kDepthTile);
+    if (ntiles <= v->dtiles_cap) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaFree(v->dtiles);
+    v->dtiles = nullptr;
+    v->dtiles_cap = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
+    if (e == cudaSuccess) v->dtiles_cap = ntiles;
+    return e;
+}
+
+cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
+    const int64_t ntiles = (int64_t)((K.width + kDepthTile - 1) / kDepthTile) * ((K.height + kDepthTile - 1) / kDepthTile);
+    if (v->visible_batch && ntiles <= v->dtiles_batch_stride) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && !v->visible_batch)
+        e = cudaMalloc(&v->visible_batch, (size_t)v->cfg.block_capacity * kMaxBatch * sizeof(VisibleBlock));
+    if (e == cudaSuccess && ntiles > v->dtiles_batch_stride) {
+        e = cudaFree(v->dtiles_batch);
+        v->dtiles_batch = nullptr;
+        v->dtiles_batch_stride = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->dtiles_batch, (size_t)ntiles * kMaxBatch * sizeof(float2));
+        if (e == cudaSuccess) v->dtiles_batch_stride = ntiles;
+    }
+    return e;
+}
+
+cudaError_t ensure_range(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
+    const int64_t npix = (int64_t)K.width * K.height;
+    if (npix <= v->range_pixels) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaFree(v->range);
+    v->range = nullptr;
+    v->range_pixels = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)npix * sizeof(unsigned int));
+    if (e == cudaSuccess) v->range_pixels = npix;
+    return e;
+}
+
+bool pose_valid(const double* pose) { return pose_ok(pose); }
+bool intrinsics_valid(const tsdf_intrinsics* K) { return intr_ok(K); }
 
 }  // namespace tsdf
 
@@ -287,18 +336,8 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const float* depth, const float* vari
                            const double pose_wc[16], void* stream) {
     if (!v || !depth || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t ntiles = (int64_t)((K->width + tsdf::kDepthTile - 1) / tsdf::kDepthTile) *
-                           ((K->height + tsdf::kDepthTile - 1) / tsdf::kDepthTile);
-    if (ntiles > v->dtiles_cap) {
-        // grow the depth tile buffer (synchronising: done once per new image size)
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) e = cudaFree(v->dtiles);
-        v->dtiles = nullptr;
-        v->dtiles_cap = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
-        if (e != cudaSuccess) return fail_cuda(v, e);
-        v->dtiles_cap = ntiles;
-    }
+    const cudaError_t eb = tsdf::ensure_dtiles(v, *K, st);
+    if (eb != cudaSuccess) return fail_cuda(v, eb);
     const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     v->last_stream = st;
     const tsdf_status s = fail_cuda(v, tsdf::launch_integrate(v, depth, variance, p, st));
@@ -306,21 +345,41 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const float* depth, const float* vari
     return s;
 }
 
+tsdf_status tsdf_integrate_batch(tsdf_volume* v, int32_t K, const float* const* depth,
+                                 const float* const* variance, const tsdf_intrinsics* Kin, const double* poses_wc,
+                                 void* stream) {
+    if (!v || K < 1 || K > tsdf::kMaxBatch || !depth || !intr_ok(Kin) || !poses_wc) return TSDF_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (!depth[k] || !pose_ok(poses_wc + 16 * k)) return TSDF_ERR_INVALID_ARG;
+        if (variance && !variance[k]) return TSDF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const cudaError_t eb = tsdf::ensure_batch(v, *Kin, st);
+    if (eb != cudaSuccess) return fail_cuda(v, eb);
+    v->last_stream = st;
+    tsdf::BatchParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.K = K;
+    bp.f0 = (int)v->frame;
+    for (int k = 0; k < K; ++k) {
+        const AllocParams ap = tsdf::make_alloc_params(v, *Kin, poses_wc + 16 * k);
+        const cudaError_t e = tsdf::launch_allocate(v, depth[k], ap, (int)v->frame + k, st);
+        if (e != cudaSuccess) return fail_cuda(v, e);
+        bp.fp[k] = tsdf::make_frame_params(v, *Kin, poses_wc + 16 * k);
+        bp.depth[k] = depth[k];
+        bp.var[k] = variance ? variance[k] : nullptr;
+    }
+    const tsdf_status s = fail_cuda(v, tsdf::launch_integrate_batch(v, bp, st));
+    if (s == TSDF_OK) v->frame += K;
+    return s;
+}
+
 tsdf_status tsdf_raycast(tsdf_volume* v, const tsdf_intrinsics* K, const double pose_wc[16], float* depth_out,
                          float* normal_out, float* vertex_out, void* stream) {
     if (!v || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
-    const int64_t npix = (int64_t)K->width * K->height;
     cudaStream_t st = (cudaStream_t)stream;
-    if (npix > v->range_pixels) {
-        // grow the range maps (synchronising: done once per new image size)
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) e = cudaFree(v->range);
-        v->range = nullptr;
-        v->range_pixels = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)npix * sizeof(unsigned int));
-        if (e != cudaSuccess) return fail_cuda(v, e);
-        v->range_pixels = npix;
-    }
+    const cudaError_t eb = tsdf::ensure_range(v, *K, st);
+    if (eb != cudaSuccess) return fail_cuda(v, eb);
     const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     v->last_stream = st;
     return fail_cuda(v, tsdf::launch_raycast(v, p, depth_out, normal_out, vertex_out, st));

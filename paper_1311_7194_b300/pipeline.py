@@ -18,9 +18,13 @@ from . import tsdf
 
 
 class FusionPipeline:
-    def __init__(self, volume: tsdf.Volume, intr, device: Optional[torch.device] = None):
+    """``graph=True`` runs each step as one CUDA graph launch (tsdf_graph_*):
+    the same results, without per-kernel launch gaps."""
+
+    def __init__(self, volume: tsdf.Volume, intr, device: Optional[torch.device] = None, graph: bool = False):
         self.volume = volume
         self.intr = intr
+        self.graph = tsdf.Graph(volume, intr, 1) if graph else None
         dev = device or torch.device("cuda", torch.cuda.current_device())
         H, W = intr.height, intr.width
         self.depth_map = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -35,6 +39,9 @@ class FusionPipeline:
 
     def step(self, depth: torch.Tensor, pose, variance: Optional[torch.Tensor] = None, stream=None):
         """Fuse one device depth map at ``pose`` and raycast the model at ``pose``."""
+        if self.graph is not None:
+            self.graph.launch([depth], [pose], self.maps, None if variance is None else [variance], stream)
+            return
         self.volume.allocate(depth, self.intr, pose, stream)
         self.volume.integrate(depth, self.intr, pose, variance, stream)
         self.volume.raycast(self.intr, pose, out=self.maps, stream=stream)

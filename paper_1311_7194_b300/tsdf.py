@@ -21,7 +21,9 @@ STORAGE_F32 = 0
 
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
-            "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_raycast", "tsdf_raycast_noalloc",
+            "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
+            "tsdf_raycast_noalloc", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
+            "tsdf_graph_set_events", "tsdf_graph_destroy",
             "tsdf_quadratic_variance",
             "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
 
@@ -83,8 +85,15 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_reset": (ctypes.c_int, [_P, _P]),
         "tsdf_allocate": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
         "tsdf_integrate": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Intrinsics), _PD, _P]),
+        "tsdf_integrate_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                                ctypes.POINTER(Intrinsics), _PD, _P]),
         "tsdf_raycast": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
         "tsdf_raycast_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
+        "tsdf_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Intrinsics), ctypes.POINTER(_P)]),
+        "tsdf_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
+        "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
+        "tsdf_graph_set_events": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "tsdf_graph_destroy": (None, [_P]),
         "tsdf_quadratic_variance": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
         "tsdf_get_status": (ctypes.c_int, [_P]),
         "tsdf_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
@@ -219,6 +228,18 @@ class Volume:
         _check(self.lib.tsdf_integrate(self.h, _dev_ptr(depth, n, "depth"), _dev_ptr(variance, n, "variance"),
                                        ctypes.byref(K), _pose(pose), _stream(stream)), "tsdf_integrate")
 
+    def integrate_batch(self, depths, intr, poses, variances=None, stream=None):
+        """tsdf_integrate_batch: allocate and fuse K <= 8 frames in one pass
+        (bitwise equal to K sequential allocate + integrate calls)."""
+        K = intrinsics(intr)
+        n = K.width * K.height
+        k = len(depths)
+        dptr = (_P * k)(*[_dev_ptr(d, n, "depth") for d in depths])
+        vptr = None if variances is None else (_P * k)(*[_dev_ptr(v, n, "variance") for v in variances])
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(k, 16))
+        _check(self.lib.tsdf_integrate_batch(self.h, k, dptr, vptr, ctypes.byref(K),
+                                             poses.ctypes.data_as(_PD), _stream(stream)), "tsdf_integrate_batch")
+
     def fuse(self, depth, intr, pose, variance=None, stream=None):
         """Allocate then integrate one frame."""
         self.allocate(depth, intr, pose, stream)
@@ -275,6 +296,59 @@ class Volume:
         _check(self.lib.tsdf_export(self.h, cf.ctypes.data_as(_P), T.ctypes.data_as(_P) if values else None,
                                     P.ctypes.data_as(_P) if values else None, m, ctypes.byref(n)), "tsdf_export")
         return Export(cf[:, :3].copy(), cf[:, 3].copy(), T, P)
+
+
+class Graph:
+    """tsdf_graph_*: one fusion step (K frames, then a raycast at the last pose)
+    recorded as a CUDA graph and replayed per step."""
+
+    def __init__(self, volume: "Volume", intr, K: int = 1):
+        self.volume = volume
+        self.lib = volume.lib
+        self.K = int(K)
+        self.intr = intrinsics(intr)
+        h = _P()
+        _check(self.lib.tsdf_graph_create(volume.h, self.K, ctypes.byref(self.intr), ctypes.byref(h)),
+               "tsdf_graph_create")
+        self.h = h
+
+    def launch(self, depths, poses, out, variances=None, stream=None):
+        n = self.intr.width * self.intr.height
+        dptr = (_P * self.K)(*[_dev_ptr(d, n, "depth") for d in depths])
+        vptr = None if variances is None else (_P * self.K)(*[_dev_ptr(v, n, "variance") for v in variances])
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(self.K, 16))
+        d, nm, vm = out
+        _check(self.lib.tsdf_graph_launch(self.h, dptr, vptr, poses.ctypes.data_as(_PD), _dev_ptr(d, n, "depth_out"),
+                                          _dev_ptr(nm, 3 * n, "normal_out"), _dev_ptr(vm, 3 * n, "vertex_out"),
+                                          _stream(stream)), "tsdf_graph_launch")
+        return out
+
+    def set_events(self, events):
+        """Four torch.cuda.Event (timing) recorded at the stage boundaries of the
+        next launches, or None."""
+        if events is None:
+            _check(self.lib.tsdf_graph_set_events(self.h, None), "tsdf_graph_set_events")
+            return
+        for e in events:
+            if e.cuda_event == 0:
+                e.record()          # make torch create the event
+        arr = (_P * 4)(*[e.cuda_event for e in events])
+        _check(self.lib.tsdf_graph_set_events(self.h, arr), "tsdf_graph_set_events")
+
+    @property
+    def instantiations(self) -> int:
+        return int(self.lib.tsdf_graph_instantiations(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsdf_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def quadratic_variance(depth, sigma_coeff: float, out=None, stream=None):
