@@ -52,7 +52,11 @@ def parse():
     ap.add_argument("--block-capacity", type=int, default=None, help="pool size in blocks")
     ap.add_argument("--mode", choices=["graph", "direct"], default="graph",
                     help="graph: each step one CUDA graph launch; direct: one C-ABI call per stage")
-    ap.add_argument("--workload", choices=["room", "batched"], default="room",
+    ap.add_argument("--storage", choices=["f32", "f16", "snorm16"], default="f32",
+                    help="storage of T for --workload capsules")
+    ap.add_argument("--oracle-sample", type=int, default=0,
+                    help="capsules: compare this many sampled voxels with the FP64 oracle (per-voxel replay)")
+    ap.add_argument("--workload", choices=["room", "batched", "capsules"], default="room",
                     help="room: per-frame live fusion (2048^3, 1.5 mm); batched: 3000^3 grid of 1 mm voxels, "
                          "1000 frames fused K=8 per graph launch, raycast per batch")
     ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
@@ -437,12 +441,98 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_capsules(args):
+    """High-resolution small object: 1280x1024, 4096^3 grid of 0.15 mm voxels,
+    200 frames, T stored as float32, FP16 or snorm16 (P float32), one graph
+    launch per frame; optionally the error of sampled voxels against the FP64
+    oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1311_7194_b300 import build as pkg_build
+    from paper_1311_7194_b300 import synth, tsdf
+    from paper_1311_7194_b300.pipeline import FusionPipeline
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pkg_build.build()
+    storage = {"f32": tsdf.STORAGE_F32, "f16": tsdf.STORAGE_F16, "snorm16": tsdf.STORAGE_SNORM16}[args.storage]
+    n = args.frames if args.frames != 300 else 200
+    seq = synth.capsule_sequence(n_frames=n, device=dev, block_capacity=args.block_capacity or (1 << 20))
+    F, H, W = seq.depth.shape
+    depth_dev = torch.from_numpy(seq.depth).to(dev)
+    vol = tsdf.Volume.from_params(seq.volume, storage=storage)
+    pipe = FusionPipeline(vol, seq.intr, dev, graph=True)
+
+    def step():
+        vol.reset()
+        for k in range(F):
+            pipe.step(depth_dev[k], seq.poses[k])
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    vol.check()
+    clocks = ClockSampler(0)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = t0.elapsed_time(t1) / 1000.0
+    st = vol.stats()
+    bytes_per_update = 16 if storage == tsdf.STORAGE_F32 else 12
+    line = {"metric": METRIC, "value": F * args.steps / sec, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f16 T / f32 P", 2: "snorm16 T / f32 P"}[storage],
+            "data": "synthetic",
+            "config": {"workload": f"high-res small object: 1280x1024, 4096^3 grid of 0.15 mm voxels, {F} frames",
+                       "storage": args.storage, "frames_per_step": F},
+            "voxel_updates_per_s": st["voxel_updates_total"] * args.steps / sec,
+            "rays_per_s": F * H * W * args.steps / sec,
+            "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "blocks": int(st["n_blocks"])},
+            "pool_bytes_per_voxel": 4 + (4 if storage == tsdf.STORAGE_F32 else 2),
+            "algorithmic_bytes_per_update": bytes_per_update, "clocks": clk}
+    if args.oracle_sample > 0:
+        import oracle
+        oracle.build()
+        ov = oracle.OracleVolume(seq.volume, seq.intr, store_values=False)
+        for k in range(F):
+            ov.allocate(seq.depth[k], seq.poses[k], k)
+        oe = ov.export(values=False)
+        rng = np.random.default_rng(11)
+        pick = rng.choice(oe.coords.shape[0], size=min(args.oracle_sample, oe.coords.shape[0]), replace=False)
+        local = rng.integers(0, 512, size=pick.size)
+        vox = oe.coords[pick] * 8 + np.stack([local & 7, (local >> 3) & 7, local >> 6], -1)
+        T, P, amb = oracle.replay_voxels(seq.volume, seq.intr, list(seq.depth), seq.poses, vox,
+                                         oe.alloc_frame[pick], amb_px=5e-4)
+        ge = vol.export()
+        nb = seq.volume.grid_dim // 8
+        keys = ge.coords[:, 0].astype(np.int64) + nb * (ge.coords[:, 1] + nb * ge.coords[:, 2].astype(np.int64))
+        okeys = oe.coords[pick, 0].astype(np.int64) + nb * (oe.coords[pick, 1] + nb * oe.coords[pick, 2].astype(np.int64))
+        order = np.argsort(keys)
+        slot = order[np.searchsorted(keys[order], okeys)]
+        gT = ge.T[slot, local].astype(np.float64)
+        m = ~np.isnan(T) & ~amb & ~np.isnan(gT)
+        e = np.abs(gT[m] - T[m]) / seq.volume.truncation
+        line["error_vs_fp64_oracle"] = {"voxels": int(m.sum()), "max_over_delta": float(e.max()),
+                                        "rms_over_delta": float(np.sqrt((e ** 2).mean())),
+                                        "chi_mismatch": int(((np.isnan(T) != np.isnan(gT)) & ~amb).sum())}
+    pipe.graph.close()
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "capsules":
+        run_capsules(args)
     else:
         run_ours(args)
 

@@ -51,8 +51,13 @@ typedef enum {
     TSDF_ERR_OUT_OF_MEMORY = 6  /* device allocation failed in tsdf_create* */
 } tsdf_status;
 
+/* How T is held in the pool (P is always float32 and all arithmetic float32;
+ * the paper stores T in 8 bits and sizes memory at 2 bytes per voxel). */
 typedef enum {
-    TSDF_STORAGE_F32 = 0        /* T stored as float32, chi = NaN */
+    TSDF_STORAGE_F32 = 0,       /* float32, chi = NaN: 8 bytes per voxel with P */
+    TSDF_STORAGE_F16 = 1,       /* IEEE half (round to nearest even), chi = NaN: 6 bytes per voxel */
+    TSDF_STORAGE_SNORM16 = 2    /* int16 q = rint(T / (delta/32767)) in [-32767, 32767],
+                                   chi = -32768: 6 bytes per voxel */
 } tsdf_storage;
 
 /* Pinhole intrinsics of one depth map / output map. */
@@ -104,8 +109,8 @@ const char* tsdf_status_string(tsdf_status s);
  * capacity, all other settings at their defaults (section "Volumetric Scene
  * Representation": two device buffers, a block table and a pool of M^3-voxel
  * blocks, here M = 8). Allocates device memory on the current CUDA device:
- * 4 (G/8)^3 bytes of block table plus 8*512 bytes per pool block plus small
- * lists. *out receives the handle, to be freed with tsdf_destroy.
+ * 4 (G/8)^3 bytes of block table plus 8*512 (float32 storage) or 6*512 bytes
+ * per pool block plus small lists. *out receives the handle, to be freed with tsdf_destroy.
  * Errors: TSDF_ERR_INVALID_ARG (bad values, out == NULL),
  *         TSDF_ERR_OUT_OF_MEMORY, TSDF_ERR_CUDA. */
 tsdf_status tsdf_create(float voxel_size, float truncation, int64_t block_capacity,
@@ -260,7 +265,8 @@ tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
 
 /* Copy the volume to HOST buffers in pool order (synchronises). For n blocks:
  * coords_frame: n x 4 int32 (bx, by, bz, allocation frame); T: n x 512 float32
- * (chi = NaN); P: n x 512 float32 (unspecified where T is chi). Any buffer may
+ * decoded from the storage format (chi = NaN); P: n x 512 float32 (unspecified
+ * where T is chi). Any buffer may
  * be NULL; capacity is the number of blocks each buffer holds. *n_out receives
  * the pool size; if it exceeds capacity only the first capacity blocks are
  * copied. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */

@@ -194,13 +194,14 @@ __global__ void alloc_finalize_kernel(const unsigned int* __restrict__ tile_sums
 }
 
 // Fresh blocks hold chi everywhere (Fig. 4 caption: memory is allocated for a
-// block when anything but chi is to be stored in it).
-__global__ void __launch_bounds__(256) init_blocks_kernel(const Counters* __restrict__ ctr, float2* __restrict__ T,
-                                                          float2* __restrict__ P) {
+// block when anything but chi is to be stored in it). T is filled with the
+// storage format's chi pattern, one 32-bit word (1 or 2 voxels) at a time.
+__global__ void __launch_bounds__(256) init_blocks_kernel(const Counters* __restrict__ ctr,
+                                                          unsigned int* __restrict__ T, float2* __restrict__ P,
+                                                          int t_words, unsigned int chi_word) {
     const long long lo = ctr->n_blocks_prev, hi = ctr->n_blocks;
-    const float2 chi = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
     for (long long b = lo + blockIdx.x; b < hi; b += gridDim.x) {
-        T[b * 256 + threadIdx.x] = chi;
+        for (int w = threadIdx.x; w < t_words; w += blockDim.x) T[b * t_words + w] = chi_word;
         P[b * 256 + threadIdx.x] = make_float2(0.0f, 0.0f);
     }
 }
@@ -220,8 +221,13 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
                                                              v->blk_slot, v->blocks, v->cfg.block_capacity,
                                                              frame, v->nb, v->occ2, v->occ3, v->n2, v->n3);
     alloc_finalize_kernel<<<1, 32, 0, st>>>(v->tile_sums, (int)v->n_tiles, v->ctr, v->cfg.block_capacity);
-    init_blocks_kernel<<<v->num_sms * 4, 256, 0, st>>>(v->ctr, reinterpret_cast<float2*>(v->T),
-                                                       reinterpret_cast<float2*>(v->P));
+    const int bytes = storage_bytes(v->cfg.storage);
+    const unsigned chi_word = v->cfg.storage == TSDF_STORAGE_F32   ? 0x7fc00000u
+                              : v->cfg.storage == TSDF_STORAGE_F16 ? 0x7e007e00u
+                                                                   : 0x80008000u;
+    init_blocks_kernel<<<v->num_sms * 4, 256, 0, st>>>(v->ctr, reinterpret_cast<unsigned int*>(v->T),
+                                                       reinterpret_cast<float2*>(v->P), kBlockVoxels * bytes / 4,
+                                                       chi_word);
     return cudaGetLastError();
 }
 

@@ -263,10 +263,11 @@ __device__ __forceinline__ void kalman(float& T, float& P, float Tk, float pk, f
     if (fabsf(T) > delta) T = __int_as_float(0x7fc00000);
 }
 
-template <bool kVarMap>
+template <bool kVarMap, int kS>
 __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* __restrict__ ctr,
                                                                       const VisibleBlock* __restrict__ vis,
-                                                                      float* __restrict__ T, float* __restrict__ P,
+                                                                      typename Codec<kS>::E* __restrict__ T,
+                                                                      float* __restrict__ P,
                                                                       const float* __restrict__ depth,
                                                                       const float* __restrict__ var, FrameParams p) {
     const unsigned nvis = ctr->n_visible;
@@ -289,9 +290,10 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
         }
         if (!any) continue;
         const size_t off = (size_t)vb.slot * kBlockVoxels + (size_t)v0;
-        float4 t4 = *reinterpret_cast<const float4*>(T + off);
-        float4 p4 = *reinterpret_cast<const float4*>(P + off);
-        float tv[4] = {t4.x, t4.y, t4.z, t4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
+        float tv[4];
+        Codec<kS>::load4(T + off, tv, p.tscale);
+        const float4 p4 = *reinterpret_cast<const float4*>(P + off);
+        float pv[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             if (ok[e]) {
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
                 ++updates;
             }
         }
-        *reinterpret_cast<float4*>(T + off) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+        Codec<kS>::store4(T + off, tv, p.tscale);
         *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
     }
     updates = warp_sum(updates);
@@ -311,11 +313,11 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
 // before the block's allocation - and stored once. Same measurement and update
 // functions as integrate_kernel, so the result equals K sequential calls bit
 // for bit.
-template <bool kVarMap>
+template <bool kVarMap, int kS>
 __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
                                                                             const VisibleBlock* __restrict__ vis,
                                                                             const int4* __restrict__ blocks,
-                                                                            float* __restrict__ T,
+                                                                            typename Codec<kS>::E* __restrict__ T,
                                                                             float* __restrict__ P, BatchParams bp) {
     const unsigned nvis = ctr->n_visible;
     const int v0 = threadIdx.x * 4;
@@ -344,9 +346,8 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             }
             if (!any) continue;
             if (!loaded) {
-                const float4 t4 = *reinterpret_cast<const float4*>(T + off);
+                Codec<kS>::load4(T + off, tv, bp.fp[0].tscale);
                 const float4 p4 = *reinterpret_cast<const float4*>(P + off);
-                tv[0] = t4.x; tv[1] = t4.y; tv[2] = t4.z; tv[3] = t4.w;
                 pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
                 loaded = true;
             }
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             }
         }
         if (loaded) {
-            *reinterpret_cast<float4*>(T + off) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            Codec<kS>::store4(T + off, tv, bp.fp[0].tscale);
             *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
         }
     }
@@ -374,6 +375,27 @@ __global__ void reset_frame_counters(Counters* ctr) {
     ctr->voxel_updates = 0;
 }
 
+template <int kS>
+void launch_integrate_s(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+                        cudaStream_t st) {
+    auto* T = static_cast<typename Codec<kS>::E*>(v->T);
+    if (var)
+        integrate_kernel<true, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+    else
+        integrate_kernel<false, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+}
+
+template <int kS>
+void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
+    auto* T = static_cast<typename Codec<kS>::E*>(v->T);
+    if (bp.var[0])
+        integrate_batch_kernel<true, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, T,
+                                                                             v->P, bp);
+    else
+        integrate_batch_kernel<false, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, T,
+                                                                              v->P, bp);
+}
+
 }  // namespace
 
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
@@ -382,10 +404,11 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
     depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(depth, p, v->dtiles);
     cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)v->num_sms * 12;
-    if (var)
-        integrate_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
-    else
-        integrate_kernel<false><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, v->T, v->P, depth, var, p);
+    switch (v->cfg.storage) {
+        case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, var, p, grid, st); break;
+        case TSDF_STORAGE_SNORM16: launch_integrate_s<TSDF_STORAGE_SNORM16>(v, depth, var, p, grid, st); break;
+        default: launch_integrate_s<TSDF_STORAGE_F32>(v, depth, var, p, grid, st); break;
+    }
     return cudaGetLastError();
 }
 
@@ -397,12 +420,11 @@ cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaSt
     cull_batch_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, bp, v->dtiles_batch,
                                                       v->dtiles_batch_stride, v->visible_batch);
     const unsigned grid = (unsigned)v->num_sms * 12;
-    if (bp.var[0])
-        integrate_batch_kernel<true><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, v->T,
-                                                                         v->P, bp);
-    else
-        integrate_batch_kernel<false><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, v->T,
-                                                                          v->P, bp);
+    switch (v->cfg.storage) {
+        case TSDF_STORAGE_F16: launch_integrate_batch_s<TSDF_STORAGE_F16>(v, bp, grid, st); break;
+        case TSDF_STORAGE_SNORM16: launch_integrate_batch_s<TSDF_STORAGE_SNORM16>(v, bp, grid, st); break;
+        default: launch_integrate_batch_s<TSDF_STORAGE_F32>(v, bp, grid, st); break;
+    }
     return cudaGetLastError();
 }
 

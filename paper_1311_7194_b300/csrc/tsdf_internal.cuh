@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "tsdf.h"
+#include "tsdf_storage.cuh"
 
 namespace tsdf {
 
@@ -77,6 +78,7 @@ struct FrameParams {
     float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;
+    float tscale;        // snorm16 step: delta / 32767
     float zlo, zhi;      // camera z range a block must reach to matter
     float near_clip, far_clip;
     int width, height;
@@ -110,7 +112,7 @@ struct tsdf_volume {
     uint32_t* occ3;                // bit per 16^3-block cell
     int32_t n2, n3;                // cells per axis
     size_t occ2_words, occ3_words;
-    float* T;                      // [cap * 512]
+    void* T;                       // [cap * 512] in the storage format (tsdf_storage)
     float* P;                      // [cap * 512]
     tsdf::VisibleBlock* visible;   // [cap]
     int* visible_rc;               // [cap]

@@ -158,8 +158,9 @@ __device__ __forceinline__ int slot_of(const FrameParams& p, const int* __restri
     return __ldg(table + (unsigned)bx + (unsigned)p.nb * ((unsigned)by + (unsigned)p.nb * (unsigned)bz));
 }
 
-__device__ __forceinline__ float voxel(const float* __restrict__ T, int slot, int off) {
-    return slot < 0 ? __int_as_float(0x7fc00000) : __ldg(T + (size_t)slot * kBlockVoxels + off);
+template <int kS>
+__device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__ T, int slot, int off, float scale) {
+    return slot < 0 ? __int_as_float(0x7fc00000) : Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, scale);
 }
 
 // Trilinear T at voxel-space point q. Returns 0 = defined (value in *f),
@@ -169,9 +170,10 @@ __device__ __forceinline__ float voxel(const float* __restrict__ T, int slot, in
 // The 8 corners are fetched by the same instructions whether or not the cell
 // crosses a block face (only the extra block lookups are conditional), which
 // keeps the lanes of a warp together.
+template <int kS>
 __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __restrict__ table,
-                                         const float* __restrict__ T, float qx, float qy, float qz, float* f,
-                                         int* blk) {
+                                         const typename Codec<kS>::E* __restrict__ T, float qx, float qy, float qz,
+                                         float* f, int* blk) {
     const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
     const int ix = (int)fmaxf(fminf(fx0, 1e9f), -1e9f);
     const int iy = (int)fmaxf(fminf(fy0, 1e9f), -1e9f);
@@ -197,10 +199,11 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
     const int x0 = lx, x1 = ex ? 0 : lx + 1;
     const int y0 = 8 * ly, y1 = ey ? 0 : 8 * (ly + 1);
     const int z0 = 64 * lz, z1 = ez ? 0 : 64 * (lz + 1);
-    const float c000 = voxel(T, s000, x0 + y0 + z0), c100 = voxel(T, s100, x1 + y0 + z0);
-    const float c010 = voxel(T, s010, x0 + y1 + z0), c110 = voxel(T, s110, x1 + y1 + z0);
-    const float c001 = voxel(T, s001, x0 + y0 + z1), c101 = voxel(T, s101, x1 + y0 + z1);
-    const float c011 = voxel(T, s011, x0 + y1 + z1), c111 = voxel(T, s111, x1 + y1 + z1);
+    const float sc = p.tscale;
+    const float c000 = voxel<kS>(T, s000, x0 + y0 + z0, sc), c100 = voxel<kS>(T, s100, x1 + y0 + z0, sc);
+    const float c010 = voxel<kS>(T, s010, x0 + y1 + z0, sc), c110 = voxel<kS>(T, s110, x1 + y1 + z0, sc);
+    const float c001 = voxel<kS>(T, s001, x0 + y0 + z1, sc), c101 = voxel<kS>(T, s101, x1 + y0 + z1, sc);
+    const float c011 = voxel<kS>(T, s011, x0 + y1 + z1, sc), c111 = voxel<kS>(T, s111, x1 + y1 + z1, sc);
     const float tx = qx - fx0, ty = qy - fy0, tz = qz - fz0;
     const float c00 = __fmaf_rn(tx, c100 - c000, c000);
     const float c10 = __fmaf_rn(tx, c110 - c010, c010);
@@ -242,9 +245,11 @@ __device__ __forceinline__ float empty_exit(const FrameParams& p, const unsigned
     return ze;
 }
 
+template <int kS>
 __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const unsigned int* __restrict__ near_,
                                                       const unsigned int* __restrict__ far_,
-                                                      const int* __restrict__ table, const float* __restrict__ T,
+                                                      const int* __restrict__ table,
+                                                      const typename Codec<kS>::E* __restrict__ T,
                                                       const unsigned int* __restrict__ occ2,
                                                       const unsigned int* __restrict__ occ3,
                                                       float* __restrict__ depth_out, float* __restrict__ normal_out,
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
             float zprev_any = z, zstep = h;   // last sample taken and the step since
             int blk[3];
             for (int it = 0; it < kMaxMarch && z <= zend; ++it) {
-                const int st = trilinear(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
+                const int st = trilinear<kS>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
                                          __fmaf_rn(z, dqz, p.q0[2]), &f, blk);
                 if (st == 2) {
                     // everything before the empty cell's exit is undefined
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                         const float zq = j == kFine ? z : z - back + (float)j * (back / (float)kFine);
                         float fq = f;
                         const int sq = j == kFine ? 0
-                                                  : trilinear(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
+                                                  : trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
                                                               __fmaf_rn(zq, dqy, p.q0[1]), __fmaf_rn(zq, dqz, p.q0[2]),
                                                               &fq, blk);
                         if (sq != 0) {
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                 zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
                 for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
                     float fs;
-                    if (trilinear(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
+                    if (trilinear<kS>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
                                   __fmaf_rn(zs, dqz, p.q0[2]), &fs, blk) != 0)
                         break;
                     if (fs > 0.0f) {
@@ -364,12 +369,12 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                             qz = __fmaf_rn(zs, dqz, p.q0[2]);
                 float fp[3], fm[3];
                 bool ok = true;
-                ok = ok && trilinear(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk) == 0;
-                ok = ok && trilinear(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk) == 0;
-                ok = ok && trilinear(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk) == 0;
-                ok = ok && trilinear(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk) == 0;
-                ok = ok && trilinear(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk) == 0;
-                ok = ok && trilinear(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk) == 0;
+                ok = ok && trilinear<kS>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk) == 0;
                 if (ok) {
                     float g[3] = {fp[0] - fm[0], fp[1] - fm[1], fp[2] - fm[2]};
                     const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
@@ -405,6 +410,30 @@ __global__ void reset_rc_counters(Counters* ctr) {
     ctr->rays_hit = 0;
 }
 
+template <int kS>
+void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
+                    float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
+    raycast_kernel<kS><<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot,
+                                             static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3,
+                                             depth_out, normal_out, vertex_out, v->ctr);
+}
+
+void launch_march(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
+                  float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    switch (v->cfg.storage) {
+        case TSDF_STORAGE_F16:
+            launch_march_s<TSDF_STORAGE_F16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            break;
+        case TSDF_STORAGE_SNORM16:
+            launch_march_s<TSDF_STORAGE_SNORM16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            break;
+        default:
+            launch_march_s<TSDF_STORAGE_F32>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            break;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out, float* normal_out,
@@ -417,9 +446,7 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
     rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
     raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
-    const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
-    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, v->occ2, v->occ3, depth_out, normal_out,
-                                         vertex_out, v->ctr);
+    launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
 
@@ -431,9 +458,7 @@ cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned
     range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
     rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
     raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
-    const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
-    raycast_kernel<<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot, v->T, v->occ2, v->occ3, depth_out, normal_out,
-                                         vertex_out, v->ctr);
+    launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,31 @@ bool intr_ok(const tsdf_intrinsics* K) {
     return (int64_t)K->width * (int64_t)K->height < (int64_t)1 << 31;
 }
 
+// IEEE half -> float for exports of TSDF_STORAGE_F16 volumes.
+float half_to_float(uint16_t h) {
+    const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+    const uint32_t ex = (h >> 10) & 0x1fu, man = h & 0x3ffu;
+    uint32_t bits;
+    if (ex == 0x1fu) {
+        bits = sign | 0x7f800000u | (man << 13);          // inf / NaN
+    } else if (ex != 0) {
+        bits = sign | ((ex + 112u) << 23) | (man << 13);   // normal
+    } else if (man == 0) {
+        bits = sign;                                         // zero
+    } else {                                                 // subnormal: renormalise
+        int e = -1;
+        uint32_t m = man;
+        do {
+            m <<= 1;
+            ++e;
+        } while (!(m & 0x400u));
+        bits = sign | ((uint32_t)(112 - e) << 23) | ((m & 0x3ffu) << 13);
+    }
+    float f;
+    std::memcpy(&f, &bits, sizeof(f));
+    return f;
+}
+
 tsdf_status fail_cuda(tsdf_volume* v, cudaError_t e) {
     if (e == cudaSuccess) return TSDF_OK;
     if (v && v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;
@@ -120,6 +145,7 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.delta = v->cfg.truncation;
     p.Q = v->cfg.process_variance;
     p.sigma_coeff = v->cfg.sigma_coeff;
+    p.tscale = (float)((double)v->cfg.truncation / 32767.0);
     const double dl = 1.01 * (double)v->cfg.truncation;
     p.zlo = (float)((double)v->cfg.depth_min - dl);
     p.zhi = (float)((double)v->cfg.depth_max + dl);
@@ -231,7 +257,8 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
         return TSDF_ERR_INVALID_ARG;
     if (!(finite_pos(c.raycast_near) && c.raycast_far > c.raycast_near && std::isfinite(c.raycast_far)))
         return TSDF_ERR_INVALID_ARG;
-    if (c.storage != TSDF_STORAGE_F32) return TSDF_ERR_INVALID_ARG;
+    if (c.storage != TSDF_STORAGE_F32 && c.storage != TSDF_STORAGE_F16 && c.storage != TSDF_STORAGE_SNORM16)
+        return TSDF_ERR_INVALID_ARG;
     if (c.alloc_half_samples < 0 || c.alloc_half_samples > 4096) return TSDF_ERR_INVALID_ARG;
     for (int r = 0; r < 3; ++r)
         if (!std::isfinite(c.origin[r])) return TSDF_ERR_INVALID_ARG;
@@ -264,7 +291,7 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     ok = ok && cudaMalloc(&v->blocks, cap * sizeof(int4)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->occ2, v->occ2_words * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->occ3, v->occ3_words * sizeof(uint32_t)) == cudaSuccess;
-    ok = ok && cudaMalloc(&v->T, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&v->T, cap * tsdf::kBlockVoxels * tsdf::storage_bytes(c.storage)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->P, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->visible, cap * sizeof(tsdf::VisibleBlock)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->visible_rc, cap * sizeof(int)) == cudaSuccess;
@@ -437,7 +464,22 @@ tsdf_status tsdf_export(tsdf_volume* v, int32_t* coords_frame, float* T, float* 
     const size_t m = (size_t)(n < capacity ? n : capacity);
     if (m == 0) return TSDF_OK;
     if (coords_frame) e = cudaMemcpy(coords_frame, v->blocks, m * sizeof(int4), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && T) e = cudaMemcpy(T, v->T, m * tsdf::kBlockVoxels * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && T) {
+        const size_t nv = m * tsdf::kBlockVoxels;
+        if (v->cfg.storage == TSDF_STORAGE_F32) {
+            e = cudaMemcpy(T, v->T, nv * sizeof(float), cudaMemcpyDeviceToHost);
+        } else {
+            // 16-bit formats: copy the raw halves / snorm codes, decode on the host
+            uint16_t* raw = (uint16_t*)std::malloc(nv * sizeof(uint16_t));
+            if (!raw) return TSDF_ERR_OUT_OF_MEMORY;
+            e = cudaMemcpy(raw, v->T, nv * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+            const float scale = (float)((double)v->cfg.truncation / 32767.0);
+            for (size_t i = 0; e == cudaSuccess && i < nv; ++i)
+                T[i] = v->cfg.storage == TSDF_STORAGE_F16 ? half_to_float(raw[i])
+                       : raw[i] == 0x8000u ? std::nanf("") : (float)(int16_t)raw[i] * scale;
+            std::free(raw);
+        }
+    }
     if (e == cudaSuccess && P) e = cudaMemcpy(P, v->P, m * tsdf::kBlockVoxels * sizeof(float), cudaMemcpyDeviceToHost);
     return fail_cuda(v, e);
 }

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtsdf.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_HASH_FULL, ERR_CUDA, ERR_NOT_READY, ERR_OUT_OF_MEMORY = range(7)
-STORAGE_F32 = 0
+STORAGE_F32, STORAGE_F16, STORAGE_SNORM16 = 0, 1, 2
 
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
