@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--block-capacity", type=int, default=None, help="pool size in blocks")
     ap.add_argument("--mode", choices=["graph", "direct"], default="graph",
                     help="graph: each step one CUDA graph launch; direct: one C-ABI call per stage")
@@ -232,6 +233,12 @@ def run_ours(args):
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume)
+    tuned = None
+    if not args.no_autotune:
+        # launch shapes picked on the first frames (results do not depend on them)
+        n_tune = min(20, F)
+        tuned, _ = vol.autotune([depth_dev[k] for k in range(n_tune)], seq.intr, seq.poses[:n_tune],
+                                os.environ.get("TSDF_AUTOTUNE_CACHE"))
     pipe = FusionPipeline(vol, seq.intr, dev, graph=args.mode == "graph")
     stream = torch.cuda.current_stream()
 
@@ -329,6 +336,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "frames_per_step": F, "width": W, "height": H, "grid_dim": 2048,
                        "voxel_size_m": 1.5e-3, "block_capacity": int(seq.volume.block_capacity),
                        "launch": "one CUDA graph per frame" if args.mode == "graph" else "one C-ABI call per stage",
+                       "launch_shape": tuned or vol.launch_config(),
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step"},
             "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,

@@ -56,8 +56,8 @@ typedef enum {
 typedef enum {
     TSDF_STORAGE_F32 = 0,       /* float32, chi = NaN: 8 bytes per voxel with P */
     TSDF_STORAGE_F16 = 1,       /* IEEE half (round to nearest even), chi = NaN: 6 bytes per voxel */
-    TSDF_STORAGE_SNORM16 = 2    /* int16 q = rint(T / (delta/32767)) in [-32767, 32767],
-                                   chi = -32768: 6 bytes per voxel */
+    TSDF_STORAGE_SNORM16 = 2    /* int16 q = rint(T * (32767/delta)) in [-32767, 32767],
+                                   T = q * (delta/32767), chi = -32768: 6 bytes per voxel */
 } tsdf_storage;
 
 /* Pinhole intrinsics of one depth map / output map. */
@@ -248,6 +248,32 @@ int64_t tsdf_graph_instantiations(const tsdf_graph* g);
  * the end of the step; NULL (or NULL entries) records none. */
 tsdf_status tsdf_graph_set_events(tsdf_graph* g, void* const events[4]);
 void tsdf_graph_destroy(tsdf_graph* g);
+
+/* Launch shapes (no counterpart in the paper; none changes any result, only
+ * speed): integrate voxels per thread (4 or 8) and persistent CTAs per SM
+ * (1..32); raycast pixel tile per CTA (16x8, 8x8, 32x4, 8x16 or 16x16).
+ * Defaults: 4, 12, 16x8. */
+typedef struct {
+    int32_t integrate_voxels_per_thread;
+    int32_t integrate_ctas_per_sm;
+    int32_t raycast_tile_w, raycast_tile_h;
+} tsdf_launch_config;
+tsdf_status tsdf_get_launch_config(const tsdf_volume* vol, tsdf_launch_config* out);
+/* TSDF_ERR_INVALID_ARG for a shape outside the lists above. */
+tsdf_status tsdf_set_launch_config(tsdf_volume* vol, const tsdf_launch_config* cfg);
+
+/* Autotuner: time every launch shape on the caller's frames (n device depth
+ * maps, host poses n*16 doubles, shared intrinsics K) - integrate on the
+ * frames fused from an empty volume, raycast at each frame's pose - keep the
+ * fastest, and record it in the JSON-lines file cache_path (may be NULL) under
+ * a key of GPU name, image size, grid size and storage. When the file already
+ * holds the key, the cached shape is set without timing and *from_cache = 1.
+ * Empties the volume (tsdf_reset) when done: tune before fusing. Allocates
+ * and synchronises; not for use under stream capture. *out (may be NULL)
+ * receives the chosen shape. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_autotune(tsdf_volume* vol, int32_t n, const float* const* depth, const tsdf_intrinsics* K,
+                          const double* poses_wc, const char* cache_path, tsdf_launch_config* out,
+                          int32_t* from_cache);
 
 /* Per-pixel measurement variance of a sensor whose deviation grows
  * quadratically with depth (Introduction; the text before Alg. 3):

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsdf.so")
-SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu", "tsdf_graph.cu"]
+SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu", "tsdf_graph.cu",
+           "tsdf_autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # No FMA contraction: every fused multiply-add is written out (__fmaf_rn), so the
 # allocation arithmetic and the Kalman update are the same op sequence wherever
@@ -37,7 +38,8 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "tsdf_internal.cuh"), os.path.join(INCLUDE, "tsdf.h")]
+    files += [os.path.join(CSRC, "tsdf_internal.cuh"), os.path.join(CSRC, "tsdf_storage.cuh"),
+              os.path.join(INCLUDE, "tsdf.h")]
     return files
 
 

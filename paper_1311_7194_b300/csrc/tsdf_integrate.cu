@@ -263,15 +263,16 @@ __device__ __forceinline__ void kalman(float& T, float& P, float Tk, float pk, f
     if (fabsf(T) > delta) T = __int_as_float(0x7fc00000);
 }
 
-template <bool kVarMap, int kS>
-__global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* __restrict__ ctr,
-                                                                      const VisibleBlock* __restrict__ vis,
-                                                                      typename Codec<kS>::E* __restrict__ T,
-                                                                      float* __restrict__ P,
-                                                                      const float* __restrict__ depth,
-                                                                      const float* __restrict__ var, FrameParams p) {
+template <bool kVarMap, int kS, int kVPT>
+__global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters* __restrict__ ctr,
+                                                                        const VisibleBlock* __restrict__ vis,
+                                                                        typename Codec<kS>::E* __restrict__ T,
+                                                                        float* __restrict__ P,
+                                                                        const float* __restrict__ depth,
+                                                                        const float* __restrict__ var, FrameParams p) {
+    static_assert(kVPT == 4 || kVPT == 8, "a thread owns 4 or 8 consecutive voxels of an x row");
     const unsigned nvis = ctr->n_visible;
-    const int v0 = threadIdx.x * 4;                       // first of this thread's 4 voxels
+    const int v0 = threadIdx.x * kVPT;                    // first of this thread's voxels
     const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
     unsigned updates = 0;
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
@@ -280,29 +281,35 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_kernel(Counters* 
         const float xr = __fmaf_rn(ly, p.cs[1], __fmaf_rn(lz, p.cs[2], vb.o[0]));
         const float yr = __fmaf_rn(ly, p.cs[4], __fmaf_rn(lz, p.cs[5], vb.o[1]));
         const float zr = __fmaf_rn(ly, p.cs[7], __fmaf_rn(lz, p.cs[8], vb.oz_lo));
-        float tk[4], pk[4];
-        bool ok[4];
+        float tk[kVPT], pk[kVPT];
+        bool ok[kVPT];
         bool any = false;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < kVPT; ++e) {
             ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
             any |= ok[e];
         }
         if (!any) continue;
         const size_t off = (size_t)vb.slot * kBlockVoxels + (size_t)v0;
-        float tv[4];
-        Codec<kS>::load4(T + off, tv, p.tscale);
-        const float4 p4 = *reinterpret_cast<const float4*>(P + off);
-        float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+        float tv[kVPT], pv[kVPT];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int g = 0; g < kVPT; g += 4) {
+            Codec<kS>::load4(T + off + g, tv + g, p.tsc);
+            const float4 p4 = *reinterpret_cast<const float4*>(P + off + g);
+            pv[g] = p4.x; pv[g + 1] = p4.y; pv[g + 2] = p4.z; pv[g + 3] = p4.w;
+        }
+#pragma unroll
+        for (int e = 0; e < kVPT; ++e) {
             if (ok[e]) {
                 kalman(tv[e], pv[e], tk[e], pk[e], p.Q, p.delta);
                 ++updates;
             }
         }
-        Codec<kS>::store4(T + off, tv, p.tscale);
-        *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+#pragma unroll
+        for (int g = 0; g < kVPT; g += 4) {
+            Codec<kS>::store4(T + off + g, tv + g, p.tsc);
+            *reinterpret_cast<float4*>(P + off + g) = make_float4(pv[g], pv[g + 1], pv[g + 2], pv[g + 3]);
+        }
     }
     updates = warp_sum(updates);
     if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             }
             if (!any) continue;
             if (!loaded) {
-                Codec<kS>::load4(T + off, tv, bp.fp[0].tscale);
+                Codec<kS>::load4(T + off, tv, bp.fp[0].tsc);
                 const float4 p4 = *reinterpret_cast<const float4*>(P + off);
                 pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
                 loaded = true;
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             }
         }
         if (loaded) {
-            Codec<kS>::store4(T + off, tv, bp.fp[0].tscale);
+            Codec<kS>::store4(T + off, tv, bp.fp[0].tsc);
             *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
         }
     }
@@ -375,14 +382,24 @@ __global__ void reset_frame_counters(Counters* ctr) {
     ctr->voxel_updates = 0;
 }
 
+template <int kS, int kVPT>
+void launch_integrate_v(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+                        cudaStream_t st) {
+    auto* T = static_cast<typename Codec<kS>::E*>(v->T);
+    constexpr int threads = kBlockVoxels / kVPT;
+    if (var)
+        integrate_kernel<true, kS, kVPT><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+    else
+        integrate_kernel<false, kS, kVPT><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+}
+
 template <int kS>
 void launch_integrate_s(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
                         cudaStream_t st) {
-    auto* T = static_cast<typename Codec<kS>::E*>(v->T);
-    if (var)
-        integrate_kernel<true, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+    if (v->lc.integrate_vpt == 8)
+        launch_integrate_v<kS, 8>(v, depth, var, p, grid, st);
     else
-        integrate_kernel<false, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+        launch_integrate_v<kS, 4>(v, depth, var, p, grid, st);
 }
 
 template <int kS>
@@ -403,7 +420,7 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
     reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
     depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(depth, p, v->dtiles);
     cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->dtiles, v->visible);
-    const unsigned grid = (unsigned)v->num_sms * 12;
+    const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, var, p, grid, st); break;
         case TSDF_STORAGE_SNORM16: launch_integrate_s<TSDF_STORAGE_SNORM16>(v, depth, var, p, grid, st); break;

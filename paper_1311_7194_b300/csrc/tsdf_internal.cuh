@@ -78,7 +78,7 @@ struct FrameParams {
     float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;
-    float tscale;        // snorm16 step: delta / 32767
+    float2 tsc;          // snorm16 scales: (delta / 32767, 32767 / delta)
     float zlo, zhi;      // camera z range a block must reach to matter
     float near_clip, far_clip;
     int width, height;
@@ -93,6 +93,13 @@ struct BatchParams {
     const float* var[kMaxBatch];
     int K;
     int f0;              // frame counter of the batch's first frame
+};
+
+// Launch shapes (chosen by tsdf_autotune; none changes any result).
+struct LaunchConfig {
+    int integrate_vpt;           // voxels per thread of the integrate kernel: 4 or 8
+    int integrate_ctas_per_sm;   // persistent integrate CTAs per SM
+    int raycast_tile_w, raycast_tile_h;   // raycast CTA tile in pixels
 };
 
 }  // namespace tsdf
@@ -127,6 +134,7 @@ struct tsdf_volume {
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host
+    tsdf::LaunchConfig lc;
 };
 
 namespace tsdf {

@@ -159,8 +159,8 @@ __device__ __forceinline__ int slot_of(const FrameParams& p, const int* __restri
 }
 
 template <int kS>
-__device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__ T, int slot, int off, float scale) {
-    return slot < 0 ? __int_as_float(0x7fc00000) : Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, scale);
+__device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__ T, int slot, int off, float2 sc) {
+    return slot < 0 ? __int_as_float(0x7fc00000) : Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, sc);
 }
 
 // Trilinear T at voxel-space point q. Returns 0 = defined (value in *f),
@@ -199,7 +199,7 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
     const int x0 = lx, x1 = ex ? 0 : lx + 1;
     const int y0 = 8 * ly, y1 = ey ? 0 : 8 * (ly + 1);
     const int z0 = 64 * lz, z1 = ez ? 0 : 64 * (lz + 1);
-    const float sc = p.tscale;
+    const float2 sc = p.tsc;
     const float c000 = voxel<kS>(T, s000, x0 + y0 + z0, sc), c100 = voxel<kS>(T, s100, x1 + y0 + z0, sc);
     const float c010 = voxel<kS>(T, s010, x0 + y1 + z0, sc), c110 = voxel<kS>(T, s110, x1 + y1 + z0, sc);
     const float c001 = voxel<kS>(T, s001, x0 + y0 + z1, sc), c101 = voxel<kS>(T, s101, x1 + y0 + z1, sc);
@@ -245,8 +245,8 @@ __device__ __forceinline__ float empty_exit(const FrameParams& p, const unsigned
     return ze;
 }
 
-template <int kS>
-__global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const unsigned int* __restrict__ near_,
+template <int kS, int kTW, int kTH>
+__global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p, const unsigned int* __restrict__ near_,
                                                       const unsigned int* __restrict__ far_,
                                                       const int* __restrict__ table,
                                                       const typename Codec<kS>::E* __restrict__ T,
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(128) raycast_kernel(const FrameParams p, const
                                                       const unsigned int* __restrict__ occ3,
                                                       float* __restrict__ depth_out, float* __restrict__ normal_out,
                                                       float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
-    const int u = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int v = blockIdx.y * 8 + (threadIdx.x >> 4);
+    const int u = blockIdx.x * kTW + (threadIdx.x % kTW);
+    const int v = blockIdx.y * kTH + (threadIdx.x / kTW);
     const bool in = u < p.width && v < p.height;
     bool hit = false;
     if (in) {
@@ -410,13 +410,31 @@ __global__ void reset_rc_counters(Counters* ctr) {
     ctr->rays_hit = 0;
 }
 
+template <int kS, int kTW, int kTH>
+void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
+                    float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    const dim3 grid((unsigned)((p.width + kTW - 1) / kTW), (unsigned)((p.height + kTH - 1) / kTH));
+    raycast_kernel<kS, kTW, kTH><<<grid, kTW * kTH, 0, st>>>(p, near_, far_, v->blk_slot,
+                                                             static_cast<const typename Codec<kS>::E*>(v->T),
+                                                             v->occ2, v->occ3, depth_out, normal_out, vertex_out,
+                                                             v->ctr);
+}
+
+// Raycast tile shapes the autotuner chooses from (pixels per CTA, width x height).
 template <int kS>
 void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
-    const dim3 grid((unsigned)((p.width + 15) / 16), (unsigned)((p.height + 7) / 8));
-    raycast_kernel<kS><<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot,
-                                             static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3,
-                                             depth_out, normal_out, vertex_out, v->ctr);
+    const int tw = v->lc.raycast_tile_w, th = v->lc.raycast_tile_h;
+    if (tw == 8 && th == 8)
+        launch_march_t<kS, 8, 8>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    else if (tw == 32 && th == 4)
+        launch_march_t<kS, 32, 4>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    else if (tw == 8 && th == 16)
+        launch_march_t<kS, 8, 16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    else if (tw == 16 && th == 16)
+        launch_march_t<kS, 16, 16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    else
+        launch_march_t<kS, 16, 8>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
 }
 
 void launch_march(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,

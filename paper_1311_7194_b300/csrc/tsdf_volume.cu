@@ -145,7 +145,7 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.delta = v->cfg.truncation;
     p.Q = v->cfg.process_variance;
     p.sigma_coeff = v->cfg.sigma_coeff;
-    p.tscale = (float)((double)v->cfg.truncation / 32767.0);
+    p.tsc = make_float2((float)((double)v->cfg.truncation / 32767.0), (float)(32767.0 / (double)v->cfg.truncation));
     const double dl = 1.01 * (double)v->cfg.truncation;
     p.zlo = (float)((double)v->cfg.depth_min - dl);
     p.zhi = (float)((double)v->cfg.depth_max + dl);
@@ -277,6 +277,7 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     v->occ2_words = ((size_t)v->n2 * v->n2 * v->n2 + 31) / 32;
     v->occ3_words = ((size_t)v->n3 * v->n3 * v->n3 + 31) / 32;
     v->host_error = TSDF_OK;
+    v->lc = tsdf::LaunchConfig{4, 12, 16, 8};
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device);
     if (e != cudaSuccess) {

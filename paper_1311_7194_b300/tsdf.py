@@ -23,7 +23,8 @@ STORAGE_F32, STORAGE_F16, STORAGE_SNORM16 = 0, 1, 2
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
             "tsdf_raycast_noalloc", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
-            "tsdf_graph_set_events", "tsdf_graph_destroy",
+            "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
+            "tsdf_autotune",
             "tsdf_quadratic_variance",
             "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
 
@@ -47,6 +48,14 @@ class Config(ctypes.Structure):
 class Intrinsics(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
                 ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("integrate_voxels_per_thread", ctypes.c_int32), ("integrate_ctas_per_sm", ctypes.c_int32),
+                ("raycast_tile_w", ctypes.c_int32), ("raycast_tile_h", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -93,6 +102,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
         "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
         "tsdf_graph_set_events": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+        "tsdf_get_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
+        "tsdf_set_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
+        "tsdf_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(Intrinsics), _PD,
+                                         ctypes.c_char_p, ctypes.POINTER(LaunchConfig), ctypes.POINTER(ctypes.c_int32)]),
         "tsdf_graph_destroy": (None, [_P]),
         "tsdf_quadratic_variance": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
         "tsdf_get_status": (ctypes.c_int, [_P]),
@@ -274,6 +287,32 @@ class Volume:
                                              _dev_ptr(v, 3 * H * W, "vertex_out"), _stream(stream)),
                "tsdf_raycast_noalloc")
         return out
+
+    def launch_config(self) -> dict:
+        c = LaunchConfig()
+        _check(self.lib.tsdf_get_launch_config(self.h, ctypes.byref(c)), "tsdf_get_launch_config")
+        return c.as_dict()
+
+    def set_launch_config(self, **kw):
+        c = LaunchConfig()
+        _check(self.lib.tsdf_get_launch_config(self.h, ctypes.byref(c)), "tsdf_get_launch_config")
+        for k, v in kw.items():
+            setattr(c, k, int(v))
+        _check(self.lib.tsdf_set_launch_config(self.h, ctypes.byref(c)), "tsdf_set_launch_config")
+
+    def autotune(self, depths, intr, poses, cache_path: Optional[str] = None):
+        """tsdf_autotune: returns (chosen launch shape, loaded_from_cache). Empties the volume."""
+        K = intrinsics(intr)
+        n = K.width * K.height
+        k = len(depths)
+        dptr = (_P * k)(*[_dev_ptr(d, n, "depth") for d in depths])
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(k, 16))
+        out = LaunchConfig()
+        hit = ctypes.c_int32(0)
+        _check(self.lib.tsdf_autotune(self.h, k, dptr, ctypes.byref(K), poses.ctypes.data_as(_PD),
+                                      None if cache_path is None else cache_path.encode(), ctypes.byref(out),
+                                      ctypes.byref(hit)), "tsdf_autotune")
+        return out.as_dict(), bool(hit.value)
 
     def status(self) -> int:
         return int(self.lib.tsdf_get_status(self.h))
