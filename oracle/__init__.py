@@ -92,6 +92,11 @@ def _load(path: Optional[str] = None) -> ctypes.CDLL:
         "ov_dense_coverage": (None, [_P, _P, _I64, _I64]),
         "ov_num_threads": (ctypes.c_int32, []),
         "ov_field": (None, [_P, ctypes.c_int64, _D, _D]),
+        "ov_mlp_param_count": (ctypes.c_int32, []),
+        "ov_mlp_features": (None, [_F, ctypes.POINTER(_Intr), ctypes.POINTER(_Params), ctypes.c_int64, _I32, _D, _U8]),
+        "ov_mlp_forward": (None, [_D, ctypes.c_int64, _D, _D]),
+        "ov_mlp_loss_grad": (None, [_D, ctypes.c_int64, _D, _D, _D, _D]),
+        "ov_mlp_variance_map": (None, [_D, _F, ctypes.POINTER(_Intr), ctypes.POINTER(_Params), _F]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +300,46 @@ class DenseOracle:
         nv, nm = ctypes.c_int64(0), ctypes.c_int64(0)
         self.lib.ov_dense_coverage(self.h, sparse.h, ctypes.byref(nv), ctypes.byref(nm))
         return int(nv.value), int(nm.value)
+
+
+class Mlp:
+    """FP64 learned-variance network (27-32-32-1, ReLU) of the oracle."""
+
+    def __init__(self, weights: np.ndarray, lib_path: Optional[str] = None):
+        self.lib = lib(lib_path)
+        self.n_params = int(self.lib.ov_mlp_param_count())
+        self.w = np.ascontiguousarray(weights, np.float64).ravel()
+        assert self.w.size == self.n_params
+
+    def features(self, depth, intr, vol, uv):
+        uv = np.ascontiguousarray(uv, np.int32).reshape(-1, 2)
+        n = uv.shape[0]
+        f = np.empty((n, 27)); valid = np.empty(n, np.uint8)
+        p = make_params(vol)
+        self.lib.ov_mlp_features(_ptr(_f32(depth), _F), ctypes.byref(make_intr(intr)), ctypes.byref(p), n,
+                                 _ptr(uv, _I32), _ptr(f, _D), _ptr(valid, _U8))
+        return f, valid.astype(bool)
+
+    def forward(self, feats):
+        x = _f64(feats).reshape(-1, 27)
+        out = np.empty(x.shape[0])
+        self.lib.ov_mlp_forward(_ptr(self.w, _D), x.shape[0], _ptr(x, _D), _ptr(out, _D))
+        return out
+
+    def loss_grad(self, feats, s):
+        x = _f64(feats).reshape(-1, 27)
+        s = _f64(s)
+        g = np.empty(self.n_params); loss = np.empty(1)
+        self.lib.ov_mlp_loss_grad(_ptr(self.w, _D), x.shape[0], _ptr(x, _D), _ptr(s, _D), _ptr(g, _D), _ptr(loss, _D))
+        return float(loss[0]), g
+
+    def variance_map(self, depth, intr, vol):
+        d = _f32(depth)
+        out = np.empty(d.shape, np.float32)
+        p = make_params(vol)
+        self.lib.ov_mlp_variance_map(_ptr(self.w, _D), _ptr(d, _F), ctypes.byref(make_intr(intr)), ctypes.byref(p),
+                                     _ptr(out, _F))
+        return out
 
 
 def num_threads() -> int:

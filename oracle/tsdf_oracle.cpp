@@ -739,6 +739,187 @@ void ov_dense_coverage(const void* dense, const void* sparse, int64_t* n_valid, 
     *n_missed = nm;
 }
 
+// --------------------------------------------------------------------------
+// Learned measurement variance (an addition to the paper: it motivates
+// per-measurement variances - deviation growing with depth, poorer data near
+// surface edges - and leaves their estimation open). A 27-32-32-1 perceptron
+// with ReLU predicts out = log(p_k / p_quad) at a pixel from
+//   f[0..24] = (D(u + d) - D(u)) / delta clamped to [-1, 1] over the 5x5
+//              neighbourhood d (row-major, dy then dx); +1 where the neighbour
+//              is outside the image or not a valid measurement,
+//   f[25]    = D(u) / 4,
+//   f[26]    = |cos| of the angle between the viewing ray and the surface
+//              normal from the depth map's central differences (0 when a
+//              4-neighbour is invalid);
+// the variance is p_quad exp(out), or p_quad when |out| > ln 4 or out is not
+// finite. Training minimises the Gaussian negative log-likelihood of fusion
+// residuals r: L = (log p + r^2 / p) / 2, i.e. (out + s exp(-out)) / 2 up to a
+// constant, s = r^2 / p_quad. Parameters, in order: W1[32][27], b1[32],
+// W2[32][32], b2[32], W3[32], b3 (1985 values).
+// --------------------------------------------------------------------------
+constexpr int kIn = 27, kHid = 32;
+constexpr int kParams = kHid * kIn + kHid + kHid * kHid + kHid + kHid + 1;
+
+int32_t ov_mlp_param_count(void) { return kParams; }
+
+// Features of n pixels (uv: n x 2); valid[k] = 0 when the centre depth is not a
+// valid measurement (the network is then not used).
+void ov_mlp_features(const float* depth, const ov_intr* in, const ov_params* p, int64_t n, const int32_t* uv,
+                     double* feat, uint8_t* valid) {
+    const double delta = (double)p->truncation;
+    auto D = [&](int64_t u, int64_t v, double* out) {
+        if (u < 0 || v < 0 || u >= in->width || v >= in->height) return false;
+        const float d = depth[v * in->width + u];
+        if (!depth_valid(d, *p)) return false;
+        *out = (double)d;
+        return true;
+    };
+    auto point = [&](int64_t u, int64_t v, double d, double P[3]) {
+        P[0] = d * ((double)u - (double)in->cx) / (double)in->fx;
+        P[1] = d * ((double)v - (double)in->cy) / (double)in->fy;
+        P[2] = d;
+    };
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t u = uv[2 * k], v = uv[2 * k + 1];
+        double* f = feat + kIn * k;
+        double d0;
+        valid[k] = D(u, v, &d0) ? 1 : 0;
+        if (!valid[k]) {
+            for (int i = 0; i < kIn; ++i) f[i] = 0.0;
+            continue;
+        }
+        int i = 0;
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx, ++i) {
+                double d;
+                f[i] = D(u + dx, v + dy, &d) ? std::fmax(-1.0, std::fmin(1.0, (d - d0) / delta)) : 1.0;
+            }
+        f[25] = d0 / 4.0;
+        double dl, dr, du, dd;
+        f[26] = 0.0;
+        if (D(u - 1, v, &dl) && D(u + 1, v, &dr) && D(u, v - 1, &du) && D(u, v + 1, &dd)) {
+            double Pl[3], Pr[3], Pu[3], Pd[3], P0[3];
+            point(u - 1, v, dl, Pl); point(u + 1, v, dr, Pr); point(u, v - 1, du, Pu); point(u, v + 1, dd, Pd);
+            point(u, v, d0, P0);
+            const double a[3] = {Pr[0] - Pl[0], Pr[1] - Pl[1], Pr[2] - Pl[2]};
+            const double b[3] = {Pd[0] - Pu[0], Pd[1] - Pu[1], Pd[2] - Pu[2]};
+            const double nn[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            const double ln = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            const double lp = std::sqrt(P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2]);
+            if (ln > 0.0 && lp > 0.0) f[26] = std::fabs(nn[0] * P0[0] + nn[1] * P0[1] + nn[2] * P0[2]) / (ln * lp);
+        }
+    }
+}
+
+namespace {
+struct MlpAct {
+    double h1[kHid], a1[kHid], h2[kHid], a2[kHid], out;
+};
+
+void mlp_forward(const double* w, const double* x, MlpAct* t) {
+    const double* W1 = w;
+    const double* b1 = W1 + kHid * kIn;
+    const double* W2 = b1 + kHid;
+    const double* b2 = W2 + kHid * kHid;
+    const double* W3 = b2 + kHid;
+    const double b3 = W3[kHid];
+    for (int j = 0; j < kHid; ++j) {
+        double acc = b1[j];
+        for (int i = 0; i < kIn; ++i) acc += W1[j * kIn + i] * x[i];
+        t->h1[j] = acc;
+        t->a1[j] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int j = 0; j < kHid; ++j) {
+        double acc = b2[j];
+        for (int i = 0; i < kHid; ++i) acc += W2[j * kHid + i] * t->a1[i];
+        t->h2[j] = acc;
+        t->a2[j] = acc > 0.0 ? acc : 0.0;
+    }
+    double acc = b3;
+    for (int j = 0; j < kHid; ++j) acc += W3[j] * t->a2[j];
+    t->out = acc;
+}
+}  // namespace
+
+void ov_mlp_forward(const double* w, int64_t n, const double* feat, double* out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        MlpAct t;
+        mlp_forward(w, feat + kIn * k, &t);
+        out[k] = t.out;
+    }
+}
+
+// Sum over the n samples of L = (out + s exp(-out)) / 2 and its gradient with
+// respect to every parameter (backpropagation, written out layer by layer).
+void ov_mlp_loss_grad(const double* w, int64_t n, const double* feat, const double* s, double* grad, double* loss) {
+    const double* W2 = w + kHid * kIn + kHid;
+    const double* W3 = W2 + kHid * kHid + kHid;
+    for (int i = 0; i < kParams; ++i) grad[i] = 0.0;
+    double total = 0.0;
+    double* gW1 = grad;
+    double* gb1 = gW1 + kHid * kIn;
+    double* gW2 = gb1 + kHid;
+    double* gb2 = gW2 + kHid * kHid;
+    double* gW3 = gb2 + kHid;
+    double* gb3 = gW3 + kHid;
+    for (int64_t k = 0; k < n; ++k) {
+        const double* x = feat + kIn * k;
+        MlpAct t;
+        mlp_forward(w, x, &t);
+        const double e = s[k] * std::exp(-t.out);
+        total += 0.5 * (t.out + e);
+        const double g = 0.5 * (1.0 - e);            // dL/dout
+        double d2[kHid], d1[kHid];
+        *gb3 += g;
+        for (int j = 0; j < kHid; ++j) {
+            gW3[j] += g * t.a2[j];
+            d2[j] = t.h2[j] > 0.0 ? g * W3[j] : 0.0;
+        }
+        for (int j = 0; j < kHid; ++j) {
+            gb2[j] += d2[j];
+            for (int i = 0; i < kHid; ++i) gW2[j * kHid + i] += d2[j] * t.a1[i];
+        }
+        for (int i = 0; i < kHid; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < kHid; ++j) acc += W2[j * kHid + i] * d2[j];
+            d1[i] = t.h1[i] > 0.0 ? acc : 0.0;
+        }
+        for (int j = 0; j < kHid; ++j) {
+            gb1[j] += d1[j];
+            for (int i = 0; i < kIn; ++i) gW1[j * kIn + i] += d1[j] * x[i];
+        }
+    }
+    *loss = total;
+}
+
+// Per-pixel variance map with the network (float output, 0 where the depth is
+// not valid): p_quad exp(out), or p_quad where |out| > ln 4 or not finite.
+void ov_mlp_variance_map(const double* w, const float* depth, const ov_intr* in, const ov_params* p, float* var) {
+    const int64_t n = (int64_t)in->width * in->height;
+    std::vector<int32_t> uv(2 * n);
+    for (int64_t k = 0; k < n; ++k) {
+        uv[2 * k] = (int32_t)(k % in->width);
+        uv[2 * k + 1] = (int32_t)(k / in->width);
+    }
+    std::vector<double> feat(kIn * n), out(n);
+    std::vector<uint8_t> valid(n);
+    ov_mlp_features(depth, in, p, n, uv.data(), feat.data(), valid.data());
+    ov_mlp_forward(w, n, feat.data(), out.data());
+    const double lim = std::log(4.0);
+    for (int64_t k = 0; k < n; ++k) {
+        if (!valid[k]) {
+            var[k] = 0.0f;
+            continue;
+        }
+        const double d = (double)depth[k];
+        const double sg = (double)p->sigma_coeff * d * d;
+        const double pq = sg * sg;
+        var[k] = (float)((std::isfinite(out[k]) && std::fabs(out[k]) <= lim) ? pq * std::exp(out[k]) : pq);
+    }
+}
+
 int32_t ov_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -408,10 +408,135 @@ def pin_sphere_raycast_analytic(lib_path=None):
     assert np.median(ang) < 6.0 and ang.max() < 15.0, (np.median(ang), ang.max())
 
 
+# ----------------------------------------------------------------------------
+# learned variance network (an addition to the paper; see the oracle)
+# ----------------------------------------------------------------------------
+
+def _bf16(x):
+    """Round float64 values to bfloat16 (nearest even) and widen back."""
+    f = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _random_mlp(rng, lib_path=None):
+    n = int(oracle.lib(lib_path).ov_mlp_param_count())
+    w = _bf16(rng.normal(0.0, 0.3, n))
+    return oracle.Mlp(w, lib_path)
+
+
+def pin_mlp_gradient_finite_differences(lib_path=None):
+    """The backward pass equals central finite differences of the summed loss
+    (out + s exp(-out)) / 2 for every bias and a sample of weights."""
+    rng = np.random.default_rng(61)
+    net = _random_mlp(rng, lib_path)
+    x = rng.uniform(-1, 1, (40, 27))
+    x[:, 25] = rng.uniform(0.1, 1.0, 40)
+    x[:, 26] = rng.uniform(0, 1, 40)
+    s = rng.uniform(0.1, 4.0, 40)
+    loss, g = net.loss_grad(x, s)
+    idx = np.concatenate([rng.choice(net.n_params, 150, replace=False), np.arange(864, 896),
+                          np.arange(1920, 1985)])
+    h = 1e-6
+    for i in idx:
+        wp, wm = net.w.copy(), net.w.copy()
+        wp[i] += h
+        wm[i] -= h
+        lp, _ = oracle.Mlp(wp, lib_path).loss_grad(x, s)
+        lm, _ = oracle.Mlp(wm, lib_path).loss_grad(x, s)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    out = net.forward(x)
+    assert abs(loss - 0.5 * (out + s * np.exp(-out)).sum()) < 1e-9 * abs(loss)
+
+
+def pin_mlp_closed_forms(lib_path=None):
+    """A network with only b3 = c outputs c everywhere; one path through the
+    depth input (W1[0][25] = W2[0][0] = W3[0] = 1) outputs D/4, and the same
+    path with a negative first weight is cut by ReLU to 0."""
+    n = int(oracle.lib(lib_path).ov_mlp_param_count())
+    rng = np.random.default_rng(62)
+    x = rng.uniform(-1, 1, (25, 27))
+    x[:, 25] = rng.uniform(0.1, 1.0, 25)
+    w = np.zeros(n)
+    w[-1] = 0.37
+    assert np.allclose(oracle.Mlp(w, lib_path).forward(x), 0.37, atol=0, rtol=1e-15)
+    w = np.zeros(n)
+    w[0 * 27 + 25] = 1.0                       # W1[0][25]
+    w[864 + 32 + 0] = 1.0                      # W2[0][0]
+    w[864 + 32 + 1024 + 32 + 0] = 1.0          # W3[0]
+    assert np.allclose(oracle.Mlp(w, lib_path).forward(x), x[:, 25], atol=1e-15)
+    w[0 * 27 + 25] = -1.0
+    assert np.allclose(oracle.Mlp(w, lib_path).forward(x), 0.0, atol=1e-15)
+
+
+def pin_mlp_features_on_planes(lib_path=None):
+    """A fronto-parallel plane gives a zero patch, D/4, and the incidence cosine
+    of the viewing ray 1/|(xn, yn, 1)|; a plane tilted by theta about the camera
+    x axis gives |n . ray| with n = (0, -sin theta, cos theta); pixels outside
+    the image or with no measurement read +1."""
+    W, H, f = 24, 18, 20.0
+    intr = synth.Intrinsics.centred(f, W, H)
+    vol = _plane_volume()
+    net = oracle.Mlp(np.zeros(int(oracle.lib(lib_path).ov_mlp_param_count())), lib_path)
+    d0 = 0.8
+    depth = np.full((H, W), d0, np.float32)
+    uv = np.array([[12, 9], [3, 4], [20, 15], [0, 0]])
+    feat, valid = net.features(depth, intr, vol, uv)
+    assert valid.all()
+    assert np.allclose(feat[:3, :25], 0.0)
+    assert np.allclose(feat[:, 25], float(np.float32(d0)) / 4)
+    xn = (uv[:3, 0] - intr.cx) / intr.fx
+    yn = (uv[:3, 1] - intr.cy) / intr.fy
+    assert np.allclose(feat[:3, 26], 1.0 / np.sqrt(1 + xn ** 2 + yn ** 2), atol=1e-6)
+    corner = feat[3, :25].reshape(5, 5)
+    assert (corner[:2, :] == 1).all() and (corner[:, :2] == 1).all() and feat[3, 26] == 0.0
+    th = 0.5
+    v, u = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    ynp = (v - intr.cy) / intr.fy
+    # plane through (0, 0, d0) with normal (0, -sin th, cos th): z = d0 / (cos th - sin th yn) * cos th
+    depth_t = (d0 * np.cos(th) / (np.cos(th) - np.sin(th) * ynp)).astype(np.float32)
+    feat, valid = net.features(depth_t, intr, vol, uv[:3])
+    nrm = np.array([0.0, -np.sin(th), np.cos(th)])
+    xn, yn = (uv[:3, 0] - intr.cx) / intr.fx, (uv[:3, 1] - intr.cy) / intr.fy
+    ray = np.stack([xn, yn, np.ones(3)], -1)
+    want = np.abs(ray @ nrm) / np.linalg.norm(ray, axis=-1)
+    assert np.allclose(feat[:, 26], want, atol=2e-4), (feat[:, 26], want)
+    dd = depth_t[:, :].astype(np.float64)
+    k = 0
+    exp_patch = np.array([np.clip((dd[uv[k, 1] + dy, uv[k, 0] + dx] - dd[uv[k, 1], uv[k, 0]]) / vol.truncation, -1, 1)
+                          for dy in range(-2, 3) for dx in range(-2, 3)])
+    assert np.allclose(feat[0, :25], exp_patch, atol=2e-6)
+    bad = depth.copy()
+    bad[9, 12] = np.nan
+    _, valid = net.features(bad, intr, vol, uv[:1])
+    assert not valid[0]
+
+
+def pin_mlp_variance_fallback(lib_path=None):
+    """Variance = p_quad exp(out): the zero network gives the quadratic model,
+    b3 = 0.5 scales it by e^0.5, and an output beyond ln 4 falls back to it."""
+    W, H = 16, 12
+    intr = synth.Intrinsics.centred(14.0, W, H)
+    vol = _plane_volume(sigma=1.5e-3)
+    depth = np.random.default_rng(63).uniform(0.45, 0.55, (H, W)).astype(np.float32)
+    depth[3, 4] = 0.0
+    n = int(oracle.lib(lib_path).ov_mlp_param_count())
+    pq = ((np.float64(np.float32(1.5e-3)) * depth.astype(np.float64) ** 2) ** 2)
+    for b3, scale in ((0.0, 1.0), (0.5, np.exp(0.5)), (2.0, 1.0), (-1.5, 1.0)):
+        w = np.zeros(n)
+        w[-1] = b3
+        var = oracle.Mlp(w, lib_path).variance_map(depth, intr, vol).astype(np.float64)
+        ok = depth > 0
+        assert np.allclose(var[ok], (pq * scale)[ok], rtol=1e-6), b3
+        assert var[3, 4] == 0.0
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
             pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
-            pin_plane_raycast_exact, pin_sphere_raycast_analytic]
+            pin_plane_raycast_exact, pin_sphere_raycast_analytic, pin_mlp_gradient_finite_differences,
+            pin_mlp_closed_forms, pin_mlp_features_on_planes, pin_mlp_variance_fallback]
 
 
 def run_all(lib_path=None) -> list:

@@ -52,6 +52,16 @@ MUTATIONS = [
      "d[r] = pose[r] * dc[0] + pose[4 + r] * dc[1] + pose[8 + r] * dc[2];"),
     ("normal_axis_permuted", "pp[r] += s;\n        pm[r] -= s;",
      "pp[(r + 1) % 3] += s;\n        pm[(r + 1) % 3] -= s;"),
+    ("mlp_relu_grad_dropped", "d2[j] = t.h2[j] > 0.0 ? g * W3[j] : 0.0;", "d2[j] = g * W3[j];"),
+    ("mlp_backward_w2_transposed", "for (int j = 0; j < kHid; ++j) acc += W2[j * kHid + i] * d2[j];",
+     "for (int j = 0; j < kHid; ++j) acc += W2[i * kHid + j] * d2[j];"),
+    ("mlp_loss_grad_sign", "const double g = 0.5 * (1.0 - e);", "const double g = 0.5 * (e - 1.0);"),
+    ("mlp_invalid_neighbour", "? std::fmax(-1.0, std::fmin(1.0, (d - d0) / delta)) : 1.0;",
+     "? std::fmax(-1.0, std::fmin(1.0, (d - d0) / delta)) : 0.0;"),
+    ("mlp_depth_feature", "f[25] = d0 / 4.0;", "f[25] = d0 / 2.0;"),
+    ("mlp_variance_exp_sign", "pq * std::exp(out[k])", "pq * std::exp(-out[k])"),
+    ("mlp_fallback_limit", "const double lim = std::log(4.0);", "const double lim = std::log(16.0);"),
+    ("mlp_first_layer_relu", "t->a1[j] = acc > 0.0 ? acc : 0.0;", "t->a1[j] = acc;"),
 ]
 
 
