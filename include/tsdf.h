@@ -275,6 +275,56 @@ tsdf_status tsdf_autotune(tsdf_volume* vol, int32_t n, const float* const* depth
                           const double* poses_wc, const char* cache_path, tsdf_launch_config* out,
                           int32_t* from_cache);
 
+/* Learned measurement variance (no counterpart in the paper, which motivates
+ * per-measurement variances - deviation growing with depth, poorer data near
+ * edges - but does not say how to estimate them). A 27-32-32-1 perceptron with
+ * ReLU, bfloat16 weights and float32 arithmetic predicts out = log(p_k/p_quad)
+ * at a pixel from
+ *   f[0..24] = (D(u+d) - D(u)) / delta clamped to [-1, 1] over the 5x5
+ *              neighbourhood (row-major), +1 where a neighbour is outside the
+ *              image or not a valid measurement,
+ *   f[25]    = D(u) / 4,
+ *   f[26]    = |cos| between the viewing ray and the normal from the depth
+ *              map's central differences (0 when a 4-neighbour is invalid);
+ * p_k = p_quad exp(out), or p_quad when |out| > ln 4 or out is not finite
+ * (p_quad = (sigma_coeff D^2)^2). Parameters (1985): W1[32][27], b1[32],
+ * W2[32][32], b2[32], W3[32], b3. */
+int32_t tsdf_mlp_param_count(void);
+/* Install (host bfloat16 bits, n = 1985) or remove (NULL / n = 0) the network;
+ * while installed, tsdf_integrate / tsdf_integrate_batch / graph steps given no
+ * variance map compute p_k with it in the same stream. */
+tsdf_status tsdf_set_variance_mlp(tsdf_volume* vol, const uint16_t* bf16_weights, int64_t n);
+/* The variance map the network gives for one depth map (w: device bfloat16
+ * weights; depth, var_out: device W*H float32; 0 where depth is invalid). The
+ * volume supplies truncation, depth range and sigma_coeff. */
+tsdf_status tsdf_mlp_variance(const tsdf_volume* vol, const uint16_t* w, const float* depth,
+                              const tsdf_intrinsics* K, float* var_out, void* stream);
+/* Features of n pixels (uv: device n x 2 int32) -> feats (device n x 27);
+ * valid (device n bytes, may be NULL): whether the centre depth is valid. */
+tsdf_status tsdf_mlp_features(const tsdf_volume* vol, const float* depth, const tsdf_intrinsics* K, int64_t n,
+                              const int32_t* uv, float* feats, uint8_t* valid, void* stream);
+/* Training pairs: for pixels where both the measured depth and the model's
+ * raycast depth pred_depth (same pose; 0 = miss) are valid and the residual
+ * r = depth - pred lies within the truncation band, append the features and
+ * s = r^2 / p_quad at *count (device counter, incremented; rows beyond max_n
+ * are counted but not written). */
+tsdf_status tsdf_mlp_harvest(const tsdf_volume* vol, const float* depth, const float* pred_depth,
+                             const tsdf_intrinsics* K, int64_t max_n, float* feats, float* s, uint32_t* count,
+                             void* stream);
+/* Network outputs for n feature rows (device). */
+tsdf_status tsdf_mlp_forward(const uint16_t* w, int64_t n, const float* feats, float* out, void* stream);
+/* Adds to grad (device, 1985 float32) the gradient, and to loss (device
+ * scalar) the value, of the summed Gaussian negative log-likelihood
+ * (out + s exp(-out)) / 2 over rows idx[0..n) of (feats, s) (idx NULL: rows
+ * 0..n). */
+tsdf_status tsdf_mlp_loss_grad(const uint16_t* w, int64_t n, const int32_t* idx, const float* feats,
+                               const float* s, float* grad, float* loss, void* stream);
+/* One Adam step on float32 master weights w32 (moments m, v) with gradient
+ * grad * grad_scale; writes the bfloat16 copy wbf16 and zeroes grad. step >= 1
+ * is the step number used for bias correction. All pointers device, 1985 each. */
+tsdf_status tsdf_mlp_adam(float* w32, uint16_t* wbf16, float* m, float* v, float* grad, float lr, float beta1,
+                          float beta2, float eps, float grad_scale, int32_t step, void* stream);
+
 /* Per-pixel measurement variance of a sensor whose deviation grows
  * quadratically with depth (Introduction; the text before Alg. 3):
  * var[i] = (sigma_coeff * depth[i]^2)^2 for valid depth > 0, else 0.

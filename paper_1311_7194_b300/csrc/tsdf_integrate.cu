@@ -418,6 +418,12 @@ void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned gr
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
                              cudaStream_t st) {
     reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
+    if (!var && v->mlp_w) {
+        // learned variance: the network's map feeds this frame's update
+        const cudaError_t e = launch_variance_mlp(v, depth, p, v->var_map, st);
+        if (e != cudaSuccess) return e;
+        var = v->var_map;
+    }
     depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(depth, p, v->dtiles);
     cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
@@ -429,8 +435,17 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st) {
+cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cudaStream_t st) {
+    BatchParams bp = bp_in;
     reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
+    if (!bp.var[0] && v->mlp_w) {
+        for (int k = 0; k < bp.K; ++k) {
+            float* vk = v->var_batch + k * v->var_batch_stride;
+            const cudaError_t e = launch_variance_mlp(v, bp.depth[k], bp.fp[k], vk, st);
+            if (e != cudaSuccess) return e;
+            bp.var[k] = vk;
+        }
+    }
     for (int k = 0; k < bp.K; ++k)
         depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(bp.depth[k], bp.fp[k],
                                                             v->dtiles_batch + k * v->dtiles_batch_stride);

@@ -17,6 +17,7 @@ constexpr int kTileThreads = 256;        // threads per scan tile (16 words each
 constexpr unsigned kErrCapacity = 1u;    // sticky device error bits
 constexpr int kDepthTile = 8;            // depth min / max tiles used by the integrate cull
 constexpr int kMaxBatch = 8;             // frames per tsdf_integrate_batch call
+constexpr int kMlpParams = 1985;         // learned-variance network: 27-32-32-1
 constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
 constexpr int kOcc3 = 16;                // occupancy level 3: cells of 16^3 blocks (128 voxels a side)
 
@@ -131,6 +132,11 @@ struct tsdf_volume {
     tsdf::VisibleBlock* visible_batch;   // [cap * kMaxBatch] per (block, frame) entries of a batch
     float2* dtiles_batch;          // [kMaxBatch * dtiles_batch_stride]
     int64_t dtiles_batch_stride;
+    void* mlp_w;                   // learned-variance weights (bfloat16, device) or null
+    float* var_map;                // variance map made by the network for one frame
+    int64_t var_cap;
+    float* var_batch;              // [kMaxBatch * var_batch_stride]
+    int64_t var_batch_stride;
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host
@@ -145,6 +151,8 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var,
                              const FrameParams& p, cudaStream_t st);
 cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st);
+cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameParams& p, float* var,
+                                cudaStream_t st);
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
 // Raycast with caller-provided near / far range maps (each W*H words).

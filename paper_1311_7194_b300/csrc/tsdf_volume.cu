@@ -93,6 +93,9 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->dtiles);
     cudaFree(v->visible_batch);
     cudaFree(v->dtiles_batch);
+    cudaFree(v->mlp_w);
+    cudaFree(v->var_map);
+    cudaFree(v->var_batch);
 }
 
 }  // namespace
@@ -166,19 +169,30 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
 // during stream capture.
 cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
     const int64_t ntiles = (int64_t)((K.width + kDepthTile - 1) / kDepthTile) * ((K.height + kDepthTile - 1) / kDepthTile);
-    if (ntiles <= v->dtiles_cap) return cudaSuccess;
+    const int64_t npix = (int64_t)K.width * K.height;
+    if (ntiles <= v->dtiles_cap && npix <= v->var_cap) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaFree(v->dtiles);
-    v->dtiles = nullptr;
-    v->dtiles_cap = 0;
-    if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
-    if (e == cudaSuccess) v->dtiles_cap = ntiles;
+    if (e == cudaSuccess && ntiles > v->dtiles_cap) {
+        e = cudaFree(v->dtiles);
+        v->dtiles = nullptr;
+        v->dtiles_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
+        if (e == cudaSuccess) v->dtiles_cap = ntiles;
+    }
+    if (e == cudaSuccess && npix > v->var_cap) {   // variance map of the learned model
+        e = cudaFree(v->var_map);
+        v->var_map = nullptr;
+        v->var_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->var_map, (size_t)npix * sizeof(float));
+        if (e == cudaSuccess) v->var_cap = npix;
+    }
     return e;
 }
 
 cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
     const int64_t ntiles = (int64_t)((K.width + kDepthTile - 1) / kDepthTile) * ((K.height + kDepthTile - 1) / kDepthTile);
-    if (v->visible_batch && ntiles <= v->dtiles_batch_stride) return cudaSuccess;
+    const int64_t npix = (int64_t)K.width * K.height;
+    if (v->visible_batch && ntiles <= v->dtiles_batch_stride && npix <= v->var_batch_stride) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && !v->visible_batch)
         e = cudaMalloc(&v->visible_batch, (size_t)v->cfg.block_capacity * kMaxBatch * sizeof(VisibleBlock));
@@ -188,6 +202,13 @@ cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t 
         v->dtiles_batch_stride = 0;
         if (e == cudaSuccess) e = cudaMalloc(&v->dtiles_batch, (size_t)ntiles * kMaxBatch * sizeof(float2));
         if (e == cudaSuccess) v->dtiles_batch_stride = ntiles;
+    }
+    if (e == cudaSuccess && npix > v->var_batch_stride) {
+        e = cudaFree(v->var_batch);
+        v->var_batch = nullptr;
+        v->var_batch_stride = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->var_batch, (size_t)npix * kMaxBatch * sizeof(float));
+        if (e == cudaSuccess) v->var_batch_stride = npix;
     }
     return e;
 }

@@ -287,16 +287,44 @@ def _edge_band(clean: np.ndarray, jump: float, radius: int = 2) -> np.ndarray:
     return out
 
 
+def incidence_cos(clean: np.ndarray, intr: Intrinsics) -> np.ndarray:
+    """|cos| between each pixel's ray and the surface normal of the exact depth
+    map (central differences of back-projected points; 1 where undefined)."""
+    H, W = clean.shape
+    v, u = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    z = np.where(np.isfinite(clean), clean, np.nan)
+    P = np.stack([z * (u - intr.cx) / intr.fx, z * (v - intr.cy) / intr.fy, z], -1)
+    a = np.full_like(P, np.nan)
+    b = np.full_like(P, np.nan)
+    a[:, 1:-1] = P[:, 2:] - P[:, :-2]
+    b[1:-1, :] = P[2:, :] - P[:-2, :]
+    n = np.cross(a, b)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        c = np.abs((n * P).sum(-1)) / (np.linalg.norm(n, axis=-1) * np.linalg.norm(P, axis=-1))
+    return np.where(np.isfinite(c), c, 1.0)
+
+
 def sense(clean: np.ndarray, vol: VolumeParams, rng: np.random.Generator,
-          noise: bool = True, dropout_frac: float = 0.0, jump: float = 0.0) -> np.ndarray:
-    """Noisy float32 depth from exact depth: z + N(0, (a z^2)^2), out-of-range -> 0,
-    and ``dropout_frac`` of the valid pixels dropped from the edge band."""
+          noise: bool = True, dropout_frac: float = 0.0, jump: float = 0.0, intr: Optional[Intrinsics] = None,
+          edge_gain: float = 0.0, angle_gain: float = 0.0) -> np.ndarray:
+    """Noisy float32 depth from exact depth: z + N(0, sigma^2), out-of-range -> 0,
+    and ``dropout_frac`` of the valid pixels dropped from the edge band.
+
+    sigma = a z^2 (the quadratic sensor), multiplied by (1 + edge_gain) inside the
+    edge band and by (1 + angle_gain (1 - |cos|)) with the incidence cosine, when
+    those gains are set (a sensor that is also poorer near edges and at grazing
+    angles)."""
     z = clean.copy()
     finite = np.isfinite(z)
     if noise:
         n = rng.standard_normal(z.shape)
         zf = np.where(finite, z, 0.0)
-        z = np.where(finite, zf + vol.sigma_coeff * zf * zf * n, z)
+        sigma = vol.sigma_coeff * zf * zf
+        if edge_gain:
+            sigma = sigma * np.where(_edge_band(clean, jump), 1.0 + edge_gain, 1.0)
+        if angle_gain and intr is not None:
+            sigma = sigma * (1.0 + angle_gain * (1.0 - incidence_cos(clean, intr)))
+        z = np.where(finite, zf + sigma * n, z)
     ok = np.isfinite(z) & (z >= vol.depth_min) & (z <= vol.depth_max)
     out = np.where(ok, z, 0.0).astype(np.float32)
     if dropout_frac > 0:
@@ -307,7 +335,8 @@ def sense(clean: np.ndarray, vol: VolumeParams, rng: np.random.Generator,
     return out
 
 
-def _render_all(scene, intr, poses, vol, seed, device, noise, dropout_frac, keep_clean):
+def _render_all(scene, intr, poses, vol, seed, device, noise, dropout_frac, keep_clean, edge_gain=0.0,
+                angle_gain=0.0):
     F = poses.shape[0]
     depth = np.empty((F, intr.height, intr.width), np.float32)
     clean_all = np.empty((F, intr.height, intr.width)) if keep_clean else None
@@ -315,7 +344,7 @@ def _render_all(scene, intr, poses, vol, seed, device, noise, dropout_frac, keep
         clean = render_depth(scene, intr, poses[f], device).cpu().numpy()
         rng = np.random.default_rng([seed, f, 7])
         depth[f] = sense(clean, vol, rng, noise=noise, dropout_frac=dropout_frac,
-                         jump=2.0 * vol.truncation)
+                         jump=2.0 * vol.truncation, intr=intr, edge_gain=edge_gain, angle_gain=angle_gain)
         if keep_clean:
             clean_all[f] = clean
     return depth, clean_all
@@ -380,21 +409,25 @@ def room_trajectory(seed: int, n_frames: int) -> np.ndarray:
 def room_sequence(seed: int = 1, n_frames: int = 300, width: int = 640, height: int = 480,
                   f: float = 525.0, grid_dim: int = 2048, voxel_size: float = 1.5e-3,
                   block_capacity: int = 1 << 20, noise: bool = True, dropout: float = 0.02,
-                  device="cpu", keep_clean: bool = False, origin=None) -> Sequence:
+                  device="cpu", keep_clean: bool = False, origin=None, edge_gain: float = 0.0,
+                  angle_gain: float = 0.0, sigma_coeff: float = 1.5e-3) -> Sequence:
     """Room-scale workload: ground plane + 50 primitives in a 3 m cube, 640x480,
     fx = fy = 525, 300 frames on a seeded spline, sigma = 1.5e-3 z^2, 2 % edge
     dropout, depth range [0.3, 4] m, 2048^3 grid of 1.5 mm voxels (truncation
-    5 voxels), pool of 2^20 blocks. Smaller sizes give the reduced parity cases."""
+    5 voxels), pool of 2^20 blocks. Smaller sizes give the reduced parity cases.
+    ``edge_gain`` / ``angle_gain`` select a sensor that is also noisier near depth
+    edges and at grazing incidence (the learned-variance workload)."""
     scene = room_scene(seed)
     poses = room_trajectory(seed, n_frames)
     if origin is None:
         origin = (-0.036, -0.036, -0.036)
     vol = VolumeParams(voxel_size=voxel_size, truncation=5 * voxel_size, origin=tuple(origin),
                        grid_dim=grid_dim, block_capacity=block_capacity, depth_min=0.3,
-                       depth_max=4.0, raycast_near=0.3, raycast_far=4.0, sigma_coeff=1.5e-3)
+                       depth_max=4.0, raycast_near=0.3, raycast_far=4.0, sigma_coeff=sigma_coeff)
     intr = Intrinsics(f * width / 640.0, f * width / 640.0, (width - 1) / 2.0, (height - 1) / 2.0,
                       width, height)
-    depth, clean = _render_all(scene, intr, poses, vol, seed, device, noise, dropout, keep_clean)
+    depth, clean = _render_all(scene, intr, poses, vol, seed, device, noise, dropout, keep_clean, edge_gain,
+                               angle_gain)
     return Sequence("room", seed, intr, vol, scene, poses, depth, clean)
 
 

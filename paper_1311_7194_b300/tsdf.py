@@ -24,7 +24,8 @@ EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_cr
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
             "tsdf_raycast_noalloc", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
             "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
-            "tsdf_autotune",
+            "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
+            "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
             "tsdf_quadratic_variance",
             "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
 
@@ -103,6 +104,15 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
         "tsdf_graph_set_events": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "tsdf_get_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
+        "tsdf_mlp_param_count": (ctypes.c_int32, []),
+        "tsdf_set_variance_mlp": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+        "tsdf_mlp_variance": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Intrinsics), _P, _P]),
+        "tsdf_mlp_features": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), ctypes.c_int64, _P, _P, _P, _P]),
+        "tsdf_mlp_harvest": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Intrinsics), ctypes.c_int64, _P, _P, _P, _P]),
+        "tsdf_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+        "tsdf_mlp_loss_grad": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+        "tsdf_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_int32, _P]),
         "tsdf_set_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
         "tsdf_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(Intrinsics), _PD,
                                          ctypes.c_char_p, ctypes.POINTER(LaunchConfig), ctypes.POINTER(ctypes.c_int32)]),
@@ -313,6 +323,15 @@ class Volume:
                                       None if cache_path is None else cache_path.encode(), ctypes.byref(out),
                                       ctypes.byref(hit)), "tsdf_autotune")
         return out.as_dict(), bool(hit.value)
+
+    def set_variance_mlp(self, bf16_weights):
+        """Install a learned-variance network (numpy uint16 bfloat16 bits, 1985)
+        or remove it (None)."""
+        if bf16_weights is None:
+            _check(self.lib.tsdf_set_variance_mlp(self.h, None, 0), "tsdf_set_variance_mlp")
+            return
+        w = np.ascontiguousarray(bf16_weights, np.uint16)
+        _check(self.lib.tsdf_set_variance_mlp(self.h, w.ctypes.data_as(_P), w.size), "tsdf_set_variance_mlp")
 
     def status(self) -> int:
         return int(self.lib.tsdf_get_status(self.h))

@@ -1,0 +1,189 @@
+"""Learned measurement variance on the GPU against the FP64 oracle network,
+and what training it buys.
+
+Parity: features, forward outputs, the NLL gradient (summed over samples) and
+the Adam step; the variance map the integrate stage computes; fusion with the
+network against the oracle fed its own FP64 variance map. Gain: trained on
+residuals of seeded training scenes, the network lowers the fused surface's
+error against the analytic scene of a held-out sequence."""
+import ctypes
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_1311_7194_b300 import learned_variance as lv
+from paper_1311_7194_b300 import synth, tsdf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1311_7194_b300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _random_bits(seed, scale_out=1.0):
+    w = lv.init_weights(seed)
+    rng = np.random.default_rng(seed + 50)
+    w[1952:1984] = rng.normal(0, 0.2 * scale_out, 32)      # W3
+    w[1984] = 0.1 * scale_out
+    w[864:896] = rng.normal(0, 0.1, 32)
+    return lv.bf16_bits(w)
+
+
+def _room_frame(width=160, height=120):
+    return synth.room_sequence(n_frames=2, width=width, height=height, grid_dim=512, voxel_size=6e-3,
+                               block_capacity=1 << 16, edge_gain=3.0, angle_gain=2.0)
+
+
+def test_features_match_oracle():
+    seq = _room_frame()
+    vol = tsdf.Volume.from_params(seq.volume)
+    rng = np.random.default_rng(1)
+    uv = np.stack([rng.integers(0, 160, 3000), rng.integers(0, 120, 3000)], -1).astype(np.int32)
+    uv[:5] = [[0, 0], [159, 119], [1, 1], [80, 0], [0, 60]]
+    depth = torch.from_numpy(seq.depth[0]).cuda()
+    feats = torch.empty((uv.shape[0], 27), device="cuda")
+    valid = torch.empty(uv.shape[0], dtype=torch.uint8, device="cuda")
+    uvd = torch.from_numpy(uv).cuda()
+    K = tsdf.intrinsics(seq.intr)
+    assert vol.lib.tsdf_mlp_features(vol.h, _p(depth), ctypes.byref(K), uv.shape[0], _p(uvd), _p(feats), _p(valid),
+                                     None) == tsdf.OK
+    torch.cuda.synchronize()
+    of, ov = oracle.Mlp(np.zeros(lv.N_PARAMS)).features(seq.depth[0], seq.intr, seq.volume, uv)
+    g = feats.cpu().numpy()
+    assert np.array_equal(valid.cpu().numpy().astype(bool), ov)
+    assert np.abs(g[ov] - of[ov]).max() < 2e-5, np.abs(g[ov] - of[ov]).max()
+    assert ov.sum() > 2000
+
+
+def test_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(2)
+    bits = _random_bits(3)
+    w64 = lv.bf16_values(bits).astype(np.float64)
+    n = 3000
+    x = rng.uniform(-1, 1, (n, 27)).astype(np.float32)
+    x[:, 25] = rng.uniform(0.05, 1.0, n)
+    x[:, 26] = rng.uniform(0, 1, n)
+    s = rng.exponential(1.0, n).astype(np.float32)
+    net = oracle.Mlp(w64)
+    wq = torch.from_numpy(bits.view(np.int16)).cuda()
+    xd, sd = torch.from_numpy(x).cuda(), torch.from_numpy(s).cuda()
+    out = torch.empty(n, device="cuda")
+    lib = tsdf.load()
+    assert lib.tsdf_mlp_forward(_p(wq), n, _p(xd), _p(out), None) == tsdf.OK
+    ref = net.forward(x.astype(np.float64))
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-4 * max(1.0, np.abs(ref).max())
+    grad = torch.zeros(lv.N_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    assert lib.tsdf_mlp_loss_grad(_p(wq), n, None, _p(xd), _p(sd), _p(grad), _p(loss), None) == tsdf.OK
+    L, g = net.loss_grad(x.astype(np.float64), s.astype(np.float64))
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - L) <= 1e-4 * abs(L)
+    assert np.abs(gg - g).max() <= 1e-4 * np.abs(g).max(), np.abs(gg - g).max() / np.abs(g).max()
+    # the same rows through an index list, in another order
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+    grad2 = torch.zeros(lv.N_PARAMS, device="cuda")
+    loss2 = torch.zeros(1, device="cuda")
+    assert lib.tsdf_mlp_loss_grad(_p(wq), n, _p(perm), _p(xd), _p(sd), _p(grad2), _p(loss2), None) == tsdf.OK
+    assert np.abs(grad2.cpu().numpy() - gg).max() <= 1e-4 * np.abs(g).max()
+
+
+def test_adam_step_matches_its_definition():
+    rng = np.random.default_rng(4)
+    w = rng.normal(0, 0.3, lv.N_PARAMS).astype(np.float32)
+    m = rng.normal(0, 0.01, lv.N_PARAMS).astype(np.float32)
+    v = rng.uniform(0, 1e-3, lv.N_PARAMS).astype(np.float32)
+    g = rng.normal(0, 1.0, lv.N_PARAMS).astype(np.float32)
+    t, lr, b1, b2, eps, scale = 7, 1e-3, 0.9, 0.999, 1e-8, 0.25
+    d = [torch.from_numpy(a.copy()).cuda() for a in (w, m, v, g)]
+    wq = torch.zeros(lv.N_PARAMS, dtype=torch.int16, device="cuda")
+    assert tsdf.load().tsdf_mlp_adam(_p(d[0]), _p(wq), _p(d[1]), _p(d[2]), _p(d[3]), lr, b1, b2, eps, scale, t,
+                                     None) == tsdf.OK
+    f = np.float32
+    b1f, b2f = float(f(b1)), float(f(b2))       # the constants as the kernel holds them
+    gs = g.astype(np.float64) * scale
+    m1 = b1f * m + (1 - b1f) * gs
+    v1 = b2f * v + (1 - b2f) * gs * gs
+    w1 = w - lr * (m1 / (1 - b1 ** t)) / (np.sqrt(v1 / (1 - b2 ** t)) + eps)
+    assert np.allclose(d[0].cpu().numpy(), w1, rtol=1e-5, atol=1e-7)
+    assert np.allclose(d[1].cpu().numpy(), m1, rtol=1e-5, atol=1e-7)
+    assert np.allclose(d[2].cpu().numpy(), v1, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(wq.cpu().numpy().view(np.uint16), lv.bf16_bits(d[0].cpu().numpy()))
+    assert (d[3].cpu().numpy() == 0).all()
+
+
+def test_variance_map_and_fusion_match_oracle():
+    seq = synth.sphere_sequence(n_frames=6)
+    bits = _random_bits(5, scale_out=0.5)
+    net = oracle.Mlp(lv.bf16_values(bits).astype(np.float64))
+    vol = tsdf.Volume.from_params(seq.volume)
+    vol.set_variance_mlp(bits)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, amb_px=5e-4)
+    wq = torch.from_numpy(bits.view(np.int16)).cuda()
+    K = tsdf.intrinsics(seq.intr)
+    for k in range(seq.n_frames):
+        d = torch.from_numpy(seq.depth[k]).cuda()
+        ovar = net.variance_map(seq.depth[k], seq.intr, seq.volume)
+        gvar = torch.empty_like(d)
+        assert vol.lib.tsdf_mlp_variance(vol.h, _p(wq), _p(d), ctypes.byref(K), _p(gvar), None) == tsdf.OK
+        g = gvar.cpu().numpy()
+        ok = ovar > 0
+        assert np.array_equal(g > 0, ok)
+        assert np.allclose(g[ok], ovar[ok], rtol=2e-5), np.abs(g[ok] / ovar[ok] - 1).max()
+        vol.fuse(d, seq.intr, seq.poses[k])          # network variance, computed in the integrate stage
+        ov.fuse(seq.depth[k], seq.poses[k], ovar)
+    nb = seq.volume.grid_dim // 8
+    ge, oe = vol.export(), ov.export()
+    r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
+    assert r["keys_equal"] and r["frames_equal"], r
+    _, _, gT, gP = compare.sort_by_key(ge.coords, ge.alloc_frame, ge.T, ge.P, nb)
+    v = compare.compare_values(gT, gP, oe.T, oe.P, oe.amb, seq.volume.truncation, tol_P=1e-4)
+    assert v["ok"], json.dumps(v)
+
+
+def _scenes(seeds, n_frames, **kw):
+    return [synth.room_sequence(seed=sd, n_frames=n_frames, width=320, height=240, grid_dim=1024, voxel_size=3e-3,
+                                block_capacity=1 << 18, device="cuda", **kw) for sd in seeds]
+
+
+def _fused_error(seq, bits, eval_poses):
+    vol = tsdf.Volume.from_params(seq.volume)
+    if bits is not None:
+        vol.set_variance_mlp(bits)
+    d = torch.from_numpy(seq.depth).cuda()
+    for k in range(seq.n_frames):
+        vol.fuse(d[k], seq.intr, seq.poses[k])
+    vol.check()
+    return lv.surface_error(vol, seq, eval_poses, seq.scene)
+
+
+def test_training_lowers_loss_and_surface_error():
+    """Room scenes with the quadratic sensor: trained on seeds 100-103, the
+    network's variances fuse the held-out scene (seed 1) closer to the analytic
+    surface than the quadratic model does."""
+    data = lv.harvest(_scenes((100, 101, 102, 103), 40))
+    assert data.n > 100_000, data.n
+    bits, hist = lv.train(data, steps=1500, batch=4096, lr=2e-3, seed=0)
+    untrained = lv.mean_loss(lv.bf16_bits(lv.init_weights(0)), data)
+    trained = lv.mean_loss(bits, data)
+    ev = _scenes((1,), 60)[0]
+    poses = [ev.poses[k] for k in (10, 25, 40, 55)]
+    e_quad = _fused_error(ev, None, poses)
+    e_mlp = _fused_error(ev, bits, poses)
+    print(f"samples={data.n} loss {untrained:.4f} -> {trained:.4f}; surface error quadratic "
+          f"{json.dumps(e_quad)} learned {json.dumps(e_mlp)}")
+    assert trained < 0.9 * untrained
+    assert e_mlp["mae"] < 0.95 * e_quad["mae"] and e_mlp["rms"] < e_quad["rms"]
+    assert abs(e_mlp["hits"] - e_quad["hits"]) < 0.01 * e_quad["hits"]
