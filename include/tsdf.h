@@ -251,12 +251,15 @@ void tsdf_graph_destroy(tsdf_graph* g);
 
 /* Launch shapes (no counterpart in the paper; none changes any result, only
  * speed): integrate voxels per thread (4 or 8) and persistent CTAs per SM
- * (1..32); raycast pixel tile per CTA (16x8, 8x8, 32x4, 8x16 or 16x16).
- * Defaults: 4, 12, 16x8. */
+ * (1..32); raycast pixel tile per CTA (16x8, 8x8, 32x4, 8x16 or 16x16) or the
+ * persistent raycast. Defaults: 4, 12, 16x8, not persistent. */
 typedef struct {
     int32_t integrate_voxels_per_thread;
     int32_t integrate_ctas_per_sm;
     int32_t raycast_tile_w, raycast_tile_h;
+    int32_t raycast_persistent;  /* 1: persistent raycast (lanes fetch rays and run
+                                    march / refine / normal as a state machine),
+                                    0: one thread per pixel in the tile above */
 } tsdf_launch_config;
 tsdf_status tsdf_get_launch_config(const tsdf_volume* vol, tsdf_launch_config* out);
 /* TSDF_ERR_INVALID_ARG for a shape outside the lists above. */

@@ -1,7 +1,8 @@
 // Launch-shape autotuner.
 //
 // The integrate kernel's voxels per thread (4 or 8, i.e. 128 or 64 threads per
-// 8^3 block) and persistent CTAs per SM, and the raycast kernel's pixel tile,
+// 8^3 block) and persistent CTAs per SM, and the raycast kernel's pixel tile or
+// its persistent state-machine form,
 // change how work is spread over the GPU but not a single operation on any
 // voxel or ray, so every choice gives identical results; only speed differs
 // with the scene, image size and grid. tsdf_autotune times every candidate on
@@ -57,7 +58,8 @@ bool cache_lookup(const char* path, const std::string& key, tsdf::LaunchConfig* 
         found = read_int(line, "integrate_vpt", &c.integrate_vpt) &&
                 read_int(line, "integrate_ctas_per_sm", &c.integrate_ctas_per_sm) &&
                 read_int(line, "raycast_tile_w", &c.raycast_tile_w) &&
-                read_int(line, "raycast_tile_h", &c.raycast_tile_h);
+                read_int(line, "raycast_tile_h", &c.raycast_tile_h) &&
+                read_int(line, "raycast_persistent", &c.raycast_persistent);
         if (found) *lc = c;
     }
     std::fclose(f);
@@ -69,14 +71,16 @@ void cache_store(const char* path, const std::string& key, const tsdf::LaunchCon
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"integrate_vpt\": %d, \"integrate_ctas_per_sm\": %d, \"raycast_tile_w\": %d, "
-                 "\"raycast_tile_h\": %d, \"integrate_ms_per_frame\": %.6f, \"raycast_ms_per_frame\": %.6f}\n",
-                 key.c_str(), c.integrate_vpt, c.integrate_ctas_per_sm, c.raycast_tile_w, c.raycast_tile_h, int_ms,
-                 rc_ms);
+                 "\"raycast_tile_h\": %d, \"raycast_persistent\": %d, \"integrate_ms_per_frame\": %.6f, "
+                 "\"raycast_ms_per_frame\": %.6f}\n",
+                 key.c_str(), c.integrate_vpt, c.integrate_ctas_per_sm, c.raycast_tile_w, c.raycast_tile_h,
+                 c.raycast_persistent, int_ms, rc_ms);
     std::fclose(f);
 }
 
 bool valid(const tsdf_launch_config& c) {
     if (c.integrate_voxels_per_thread != 4 && c.integrate_voxels_per_thread != 8) return false;
+    if (c.raycast_persistent != 0 && c.raycast_persistent != 1) return false;
     if (c.integrate_ctas_per_sm < 1 || c.integrate_ctas_per_sm > 32) return false;
     for (const auto& t : kTiles)
         if (t[0] == c.raycast_tile_w && t[1] == c.raycast_tile_h) return true;
@@ -93,13 +97,14 @@ tsdf_status tsdf_get_launch_config(const tsdf_volume* v, tsdf_launch_config* out
     out->integrate_ctas_per_sm = v->lc.integrate_ctas_per_sm;
     out->raycast_tile_w = v->lc.raycast_tile_w;
     out->raycast_tile_h = v->lc.raycast_tile_h;
+    out->raycast_persistent = v->lc.raycast_persistent;
     return TSDF_OK;
 }
 
 tsdf_status tsdf_set_launch_config(tsdf_volume* v, const tsdf_launch_config* c) {
     if (!v || !c || !valid(*c)) return TSDF_ERR_INVALID_ARG;
     v->lc = tsdf::LaunchConfig{c->integrate_voxels_per_thread, c->integrate_ctas_per_sm, c->raycast_tile_w,
-                               c->raycast_tile_h};
+                               c->raycast_tile_h, c->raycast_persistent};
     return TSDF_OK;
 }
 
@@ -167,9 +172,14 @@ tsdf_status tsdf_autotune(tsdf_volume* v, int32_t n, const float* const* depth, 
     v->lc.integrate_vpt = best.integrate_vpt;
     v->lc.integrate_ctas_per_sm = best.integrate_ctas_per_sm;
     double best_rc = 1e30;
-    for (const auto& tile : kTiles) {
-        v->lc.raycast_tile_w = tile[0];
-        v->lc.raycast_tile_h = tile[1];
+    for (int cand = 0; cand <= (int)(sizeof(kTiles) / sizeof(kTiles[0])); ++cand) {
+        // every pixel-tile shape, then the persistent kernel
+        const bool persistent = cand == (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+        const int tw = persistent ? best.raycast_tile_w : kTiles[cand][0];
+        const int th = persistent ? best.raycast_tile_h : kTiles[cand][1];
+        v->lc.raycast_tile_w = tw;
+        v->lc.raycast_tile_h = th;
+        v->lc.raycast_persistent = persistent ? 1 : 0;
         double t_min = 1e30;
         for (int rep = 0; rep < 2 && status == TSDF_OK; ++rep) {
             double t = 0.0;
@@ -186,8 +196,9 @@ tsdf_status tsdf_autotune(tsdf_volume* v, int32_t n, const float* const* depth, 
         }
         if (status == TSDF_OK && t_min < best_rc) {
             best_rc = t_min;
-            best.raycast_tile_w = tile[0];
-            best.raycast_tile_h = tile[1];
+            best.raycast_tile_w = tw;
+            best.raycast_tile_h = th;
+            best.raycast_persistent = persistent ? 1 : 0;
         }
     }
     v->lc = best;

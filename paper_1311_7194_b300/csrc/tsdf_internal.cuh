@@ -37,6 +37,8 @@ struct Counters {
     unsigned long long visible_total;
     unsigned long long rays_total;
     unsigned long long rc_blocks_total;
+    unsigned int rc_next;        // next ray handed out by the persistent raycast
+    unsigned int pad2;
 };
 
 // One visible block for the integrate kernel: pool slot, the camera-space
@@ -101,6 +103,7 @@ struct LaunchConfig {
     int integrate_vpt;           // voxels per thread of the integrate kernel: 4 or 8
     int integrate_ctas_per_sm;   // persistent integrate CTAs per SM
     int raycast_tile_w, raycast_tile_h;   // raycast CTA tile in pixels
+    int raycast_persistent;      // 1: persistent state-machine raycast, 0: one thread per pixel
 };
 
 }  // namespace tsdf

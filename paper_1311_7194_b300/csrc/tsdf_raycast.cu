@@ -403,7 +403,267 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
     if ((threadIdx.x & 31) == 0 && hits) atomicAdd(&ctr->rays_hit, (unsigned long long)hits);
 }
 
+// Persistent variant of raycast_kernel with the same per-ray operations, so the
+// same results bit for bit. Each lane runs a small state machine - march,
+// re-scan, refine, normal - that takes exactly one trilinear sample per loop
+// iteration whatever phase its ray is in, so the lanes of a warp stay together
+// on the expensive part; a lane whose ray is finished writes it and fetches the
+// next one at once (rays handed out by a warp-aggregated atomic counter in 8x4
+// pixel tiles, which keeps neighbouring rays in a warp).
+enum RayPhase { kPhaseMarch = 0, kPhaseRescan = 1, kPhaseRefine = 2, kPhaseNormal = 3, kPhaseIdle = 4 };
+
+template <int kS>
+__global__ void __launch_bounds__(128) raycast_persistent_kernel(
+    const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
+    const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
+    const unsigned int* __restrict__ occ3, float* __restrict__ depth_out, float* __restrict__ normal_out,
+    float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const float nanf_ = __int_as_float(0x7fc00000);
+    const float h = 0.5f * p.delta;
+    const float eps = 0.02f * (float)p.s;
+    const int tiles_x = (p.width + 7) / 8;
+    const unsigned n_rays = (unsigned)(tiles_x * ((p.height + 3) / 4)) * 32u;
+    const int rtiles_x = (p.width + kRangeTile - 1) / kRangeTile;
+    unsigned hits = 0;
+
+    int phase = kPhaseIdle, pix = 0, it = 0, j = 0, side = 0, r = 0, k = 0;
+    float dqx = 0.f, dqy = 0.f, dqz = 0.f, inv[3] = {0.f, 0.f, 0.f};
+    float z = 0.f, zend = 0.f, fprev = 0.f, zprev = 0.f, zprev_any = 0.f, zstep = 0.f;
+    float back = 0.f, fl = 0.f, zl = 0.f, zt = 0.f, ft = 0.f;
+    float z1 = 0.f, f1 = 0.f, z2 = 0.f, f2 = 0.f, zs = 0.f;
+    float qh[3] = {0.f, 0.f, 0.f}, gp = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    bool prev_def = false, ldef = false, rays_left = true;
+
+    auto write_miss = [&](int px) {
+        if (depth_out) depth_out[px] = 0.0f;
+        if (normal_out) { normal_out[3 * px] = nanf_; normal_out[3 * px + 1] = nanf_; normal_out[3 * px + 2] = nanf_; }
+        if (vertex_out) { vertex_out[3 * px] = nanf_; vertex_out[3 * px + 1] = nanf_; vertex_out[3 * px + 2] = nanf_; }
+    };
+
+    for (;;) {
+        // hand out rays to idle lanes; a lane keeps drawing until it holds a ray to march
+        for (;;) {
+            const bool need = phase == kPhaseIdle && rays_left;
+            const unsigned msk = __ballot_sync(0xffffffffu, need);
+            if (!msk) break;
+            unsigned base = 0;
+            if (lane == __ffs(msk) - 1) base = atomicAdd(&ctr->rc_next, (unsigned)__popc(msk));
+            base = __shfl_sync(0xffffffffu, base, __ffs(msk) - 1);
+            if (!need) continue;
+            const unsigned idx = base + (unsigned)__popc(msk & ((1u << lane) - 1u));
+            if (idx >= n_rays) {
+                rays_left = false;
+                continue;
+            }
+            const int t = (int)(idx >> 5), w = (int)(idx & 31u);
+            const int u = (t % tiles_x) * 8 + (w & 7), v = (t / tiles_x) * 4 + (w >> 3);
+            if (u >= p.width || v >= p.height) continue;
+            pix = v * p.width + u;
+            const int tile = (v / kRangeTile) * rtiles_x + u / kRangeTile;
+            const float zn = __uint_as_float(near_[tile]), zf = __uint_as_float(far_[tile]);
+            z = fmaxf(zn, p.near_clip);
+            zend = fminf(zf, p.far_clip);
+            if (!(zn <= zf) || !(z <= zend)) {
+                write_miss(pix);
+                continue;
+            }
+            const float dcx = ((float)u - p.cx) / p.fx, dcy = ((float)v - p.cy) / p.fy;
+            dqx = p.Rs[0] * dcx + p.Rs[1] * dcy + p.Rs[2];
+            dqy = p.Rs[3] * dcx + p.Rs[4] * dcy + p.Rs[5];
+            dqz = p.Rs[6] * dcx + p.Rs[7] * dcy + p.Rs[8];
+            inv[0] = dqx != 0.0f ? 1.0f / dqx : 0.0f;
+            inv[1] = dqy != 0.0f ? 1.0f / dqy : 0.0f;
+            inv[2] = dqz != 0.0f ? 1.0f / dqz : 0.0f;
+            prev_def = false;
+            fprev = zprev = 0.0f;
+            zprev_any = z;
+            zstep = h;
+            it = 0;
+            phase = kPhaseMarch;
+        }
+        if (!__any_sync(0xffffffffu, phase != kPhaseIdle)) break;
+
+        // one sample per lane
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        bool take = phase != kPhaseIdle;
+        if (phase == kPhaseNormal) {
+            sx = qh[0] + (k == 0 ? 1.0f : k == 1 ? -1.0f : 0.0f);
+            sy = qh[1] + (k == 2 ? 1.0f : k == 3 ? -1.0f : 0.0f);
+            sz = qh[2] + (k == 4 ? 1.0f : k == 5 ? -1.0f : 0.0f);
+        } else {
+            float zq = z;
+            if (phase == kPhaseRescan) {
+                zq = zt - back + (float)j * (back / (float)kFine);
+                take = j < kFine;
+            } else if (phase == kPhaseRefine) {
+                zq = zs;
+            }
+            sx = __fmaf_rn(zq, dqx, p.q0[0]);
+            sy = __fmaf_rn(zq, dqy, p.q0[1]);
+            sz = __fmaf_rn(zq, dqz, p.q0[2]);
+        }
+        float f = 0.0f;
+        int blk[3] = {0, 0, 0};
+        const int st = take ? trilinear<kS>(p, table, T, sx, sy, sz, &f, blk) : 0;
+
+        bool finish = false, found_hit = false, enter_refine = false;
+        if (phase == kPhaseMarch) {
+            bool done = false;
+            if (st == 2) {
+                zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
+                z = zprev_any + 1e-3f * h;
+                zstep = z - zprev_any;
+                prev_def = false;
+            } else {
+                const bool def = st == 0;
+                if (def && !prev_def && f <= 0.0f && it > 0) {
+                    // re-scan the last step in the coming iterations
+                    phase = kPhaseRescan;
+                    back = fminf(zstep, z - zprev_any);
+                    zt = z;
+                    ft = f;
+                    j = 0;
+                    ldef = false;
+                    done = true;
+                } else if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
+                    z1 = zprev; f1 = fprev; z2 = z; f2 = f;
+                    enter_refine = true;
+                    done = true;
+                } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
+                    finish = true;                        // back face first: miss
+                    done = true;
+                } else {
+                    prev_def = def;
+                    fprev = f;
+                    zprev = z;
+                    zprev_any = z;
+                    zstep = def ? h : 2.0f * h;
+                    z += zstep;
+                }
+            }
+            if (!done) {
+                ++it;
+                if (!(it < kMaxMarch && z <= zend)) finish = true;
+            }
+        } else if (phase == kPhaseRescan) {
+            const float zq = j == kFine ? zt : zt - back + (float)j * (back / (float)kFine);
+            const float fq = j == kFine ? ft : f;
+            const int sq = j == kFine ? 0 : st;
+            bool resolved = false;
+            if (sq != 0) {
+                ldef = false;
+            } else if (ldef && fl > 0.0f && fq <= 0.0f) {
+                z1 = zl; f1 = fl; z2 = zq; f2 = fq;
+                enter_refine = true;
+                resolved = true;
+            } else if (ldef && fl < 0.0f && fq > 0.0f) {
+                finish = true;
+                resolved = true;
+            } else {
+                ldef = true; fl = fq; zl = zq;
+            }
+            if (!resolved && ++j > kFine) {
+                // nothing found: continue the march after the re-scanned sample
+                prev_def = true;
+                fprev = ft;
+                zprev = zt;
+                zprev_any = zt;
+                zstep = h;
+                z = zt + h;
+                phase = kPhaseMarch;
+                ++it;
+                if (!(it < kMaxMarch && z <= zend)) finish = true;
+            }
+        } else if (phase == kPhaseRefine) {
+            // the sample at zs was taken this iteration (refinement step r)
+            if (st != 0) {
+                phase = kPhaseNormal;
+            } else {
+                if (f > 0.0f) {
+                    z1 = zs; f1 = f;
+                    if (side == 1) f2 *= 0.5f;
+                    side = 1;
+                } else {
+                    z2 = zs; f2 = f;
+                    if (side == -1) f1 *= 0.5f;
+                    side = -1;
+                }
+                ++r;
+                if (f1 == f2) {
+                    phase = kPhaseNormal;
+                } else {
+                    zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
+                    if (!(r < kRefine && z2 - z1 > eps)) phase = kPhaseNormal;
+                }
+            }
+            if (phase == kPhaseNormal) {
+                qh[0] = __fmaf_rn(zs, dqx, p.q0[0]);
+                qh[1] = __fmaf_rn(zs, dqy, p.q0[1]);
+                qh[2] = __fmaf_rn(zs, dqz, p.q0[2]);
+                k = 0;
+            }
+        } else if (phase == kPhaseNormal) {
+            if (st != 0) {
+                found_hit = true;                         // hit with an undefined gradient
+                g0 = g1 = g2 = nanf_;
+                finish = true;
+            } else {
+                if ((k & 1) == 0) gp = f;
+                else if (k == 1) g0 = gp - f;
+                else if (k == 3) g1 = gp - f;
+                else g2 = gp - f;
+                if (++k == 6) {
+                    found_hit = true;
+                    finish = true;
+                }
+            }
+        }
+        if (enter_refine) {
+            // Illinois false position on [z1, z2]: first secant estimate; a
+            // bracket already narrower than eps goes straight to the normal
+            side = 0;
+            r = 0;
+            zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
+            phase = z2 - z1 > eps ? kPhaseRefine : kPhaseNormal;
+            if (phase == kPhaseNormal) {
+                qh[0] = __fmaf_rn(zs, dqx, p.q0[0]);
+                qh[1] = __fmaf_rn(zs, dqy, p.q0[1]);
+                qh[2] = __fmaf_rn(zs, dqz, p.q0[2]);
+                k = 0;
+            }
+        }
+        if (finish) {
+            if (found_hit) {
+                float n0 = nanf_, n1 = nanf_, n2 = nanf_;
+                if (!isnan(g0)) {
+                    const float gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+                    if (gn > 0.0f) {
+                        const float sg = (g0 * dqx + g1 * dqy + g2 * dqz) > 0.0f ? -1.0f : 1.0f;
+                        const float iv = sg / gn;
+                        n0 = g0 * iv; n1 = g1 * iv; n2 = g2 * iv;
+                    }
+                }
+                if (depth_out) depth_out[pix] = zs;
+                if (normal_out) { normal_out[3 * pix] = n0; normal_out[3 * pix + 1] = n1; normal_out[3 * pix + 2] = n2; }
+                if (vertex_out) {
+                    vertex_out[3 * pix] = (float)(p.origin[0] + (double)qh[0] * p.s);
+                    vertex_out[3 * pix + 1] = (float)(p.origin[1] + (double)qh[1] * p.s);
+                    vertex_out[3 * pix + 2] = (float)(p.origin[2] + (double)qh[2] * p.s);
+                }
+                ++hits;
+            } else {
+                write_miss(pix);
+            }
+            phase = kPhaseIdle;
+        }
+    }
+    hits = warp_sum(hits);
+    if (lane == 0 && hits) atomicAdd(&ctr->rays_hit, (unsigned long long)hits);
+}
+
 __global__ void reset_rc_counters(Counters* ctr) {
+    ctr->rc_next = 0;
     ctr->rays_total += ctr->rays_hit;
     ctr->rc_blocks_total += ctr->n_visible_rc;
     ctr->n_visible_rc = 0;
@@ -424,6 +684,19 @@ void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
 template <int kS>
 void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    if (v->lc.raycast_persistent) {
+        // exactly the CTAs that fit at once: a CTA launched later would find no rays left
+        static int per_sm = 0;
+        if (per_sm == 0 &&
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_persistent_kernel<kS>, 128, 0) !=
+                 cudaSuccess ||
+             per_sm < 1))
+            per_sm = 1;
+        raycast_persistent_kernel<kS><<<v->num_sms * per_sm, 128, 0, st>>>(
+            p, near_, far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
+            normal_out, vertex_out, v->ctr);
+        return;
+    }
     const int tw = v->lc.raycast_tile_w, th = v->lc.raycast_tile_h;
     if (tw == 8 && th == 8)
         launch_march_t<kS, 8, 8>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);

@@ -298,7 +298,7 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     v->occ2_words = ((size_t)v->n2 * v->n2 * v->n2 + 31) / 32;
     v->occ3_words = ((size_t)v->n3 * v->n3 * v->n3 + 31) / 32;
     v->host_error = TSDF_OK;
-    v->lc = tsdf::LaunchConfig{4, 12, 16, 8};
+    v->lc = tsdf::LaunchConfig{4, 12, 16, 8, 0};
     cudaError_t e = cudaGetDevice(&v->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device);
     if (e != cudaSuccess) {

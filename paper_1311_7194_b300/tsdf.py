@@ -53,7 +53,8 @@ class Intrinsics(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("integrate_voxels_per_thread", ctypes.c_int32), ("integrate_ctas_per_sm", ctypes.c_int32),
-                ("raycast_tile_w", ctypes.c_int32), ("raycast_tile_h", ctypes.c_int32)]
+                ("raycast_tile_w", ctypes.c_int32), ("raycast_tile_h", ctypes.c_int32),
+                ("raycast_persistent", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 SHAPES = [dict(integrate_voxels_per_thread=8, integrate_ctas_per_sm=4, raycast_tile_w=8, raycast_tile_h=8),
           dict(integrate_voxels_per_thread=4, integrate_ctas_per_sm=24, raycast_tile_w=32, raycast_tile_h=4),
           dict(integrate_voxels_per_thread=8, integrate_ctas_per_sm=16, raycast_tile_w=16, raycast_tile_h=16),
-          dict(integrate_voxels_per_thread=4, integrate_ctas_per_sm=1, raycast_tile_w=8, raycast_tile_h=16)]
+          dict(integrate_voxels_per_thread=4, integrate_ctas_per_sm=1, raycast_tile_w=8, raycast_tile_h=16),
+          dict(raycast_persistent=1), dict(raycast_persistent=1, integrate_voxels_per_thread=8)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,11 +55,11 @@ def test_bad_launch_shapes_are_rejected():
     seq = synth.sphere_sequence(n_frames=1)
     vol = tsdf.Volume.from_params(seq.volume)
     for bad in [dict(integrate_voxels_per_thread=2), dict(integrate_ctas_per_sm=0),
-                dict(integrate_ctas_per_sm=33), dict(raycast_tile_w=7)]:
+                dict(integrate_ctas_per_sm=33), dict(raycast_tile_w=7), dict(raycast_persistent=2)]:
         with pytest.raises(tsdf.TsdfError):
             vol.set_launch_config(**bad)
     assert vol.launch_config() == dict(integrate_voxels_per_thread=4, integrate_ctas_per_sm=12,
-                                       raycast_tile_w=16, raycast_tile_h=8)
+                                       raycast_tile_w=16, raycast_tile_h=8, raycast_persistent=0)
 
 
 def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
