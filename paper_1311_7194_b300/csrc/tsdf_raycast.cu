@@ -404,54 +404,114 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
 }
 
 // Persistent variant of raycast_kernel with the same per-ray operations, so the
-// same results bit for bit. Each lane runs a small state machine - march,
-// re-scan, refine, normal - that takes exactly one trilinear sample per loop
-// iteration whatever phase its ray is in, so the lanes of a warp stay together
-// on the expensive part; a lane whose ray is finished writes it and fetches the
-// next one at once (rays handed out by a warp-aggregated atomic counter in 8x4
-// pixel tiles, which keeps neighbouring rays in a warp).
-enum RayPhase { kPhaseMarch = 0, kPhaseRescan = 1, kPhaseRefine = 2, kPhaseNormal = 3, kPhaseIdle = 4 };
+// same results bit for bit. Lanes only march (and, rarely, re-scan): a lane
+// whose ray ends fetches the next ray at once (rays handed out by a
+// warp-aggregated atomic counter in 8x4-pixel tiles, which keeps neighbouring
+// rays in a warp), and a lane that brackets a crossing pushes the bracket to
+// its warp's queue in shared memory. When 32 brackets are queued (or no rays
+// are left) the whole warp refines them and takes their six normal samples
+// together, one bracket per lane, so neither stage runs with idle lanes and the
+// six independent normal samples are in flight at once.
+constexpr int kRcWarps = 4;          // warps per CTA
+constexpr int kQueue = 64;           // brackets per warp queue (< 32 queued + 32 pushed)
+
+// j-th of the kFine re-scan points of the step (zt - back, zt]
+__device__ __forceinline__ float zt_minus(float zt, float back, int j) {
+    return zt - back + (float)j * (back / (float)kFine);
+}
 
 template <int kS>
-__global__ void __launch_bounds__(128) raycast_persistent_kernel(
+__device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int* __restrict__ table,
+                                                 const typename Codec<kS>::E* __restrict__ T, int pix, float z1,
+                                                 float f1, float z2, float f2, float dqx, float dqy, float dqz,
+                                                 float* __restrict__ depth_out, float* __restrict__ normal_out,
+                                                 float* __restrict__ vertex_out) {
+    const float nanf_ = __int_as_float(0x7fc00000);
+    const float eps = 0.02f * (float)p.s;
+    int blk[3];
+    int side = 0;
+    float zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
+    for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
+        float fs;
+        if (trilinear<kS>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
+                          __fmaf_rn(zs, dqz, p.q0[2]), &fs, blk) != 0)
+            break;
+        if (fs > 0.0f) {
+            z1 = zs; f1 = fs;
+            if (side == 1) f2 *= 0.5f;
+            side = 1;
+        } else {
+            z2 = zs; f2 = fs;
+            if (side == -1) f1 *= 0.5f;
+            side = -1;
+        }
+        if (f1 == f2) break;
+        zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
+    }
+    const float qx = __fmaf_rn(zs, dqx, p.q0[0]), qy = __fmaf_rn(zs, dqy, p.q0[1]), qz = __fmaf_rn(zs, dqz, p.q0[2]);
+    float fp[3], fm[3];
+    const int s0 = trilinear<kS>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk);
+    const int s1 = trilinear<kS>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk);
+    const int s2 = trilinear<kS>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk);
+    const int s3 = trilinear<kS>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk);
+    const int s4 = trilinear<kS>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk);
+    const int s5 = trilinear<kS>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk);
+    float n0 = nanf_, n1 = nanf_, n2 = nanf_;
+    if ((s0 | s1 | s2 | s3 | s4 | s5) == 0) {
+        const float g0 = fp[0] - fm[0], g1 = fp[1] - fm[1], g2 = fp[2] - fm[2];
+        const float gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+        if (gn > 0.0f) {
+            const float sg = (g0 * dqx + g1 * dqy + g2 * dqz) > 0.0f ? -1.0f : 1.0f;
+            const float iv = sg / gn;
+            n0 = g0 * iv; n1 = g1 * iv; n2 = g2 * iv;
+        }
+    }
+    if (depth_out) depth_out[pix] = zs;
+    if (normal_out) { normal_out[3 * pix] = n0; normal_out[3 * pix + 1] = n1; normal_out[3 * pix + 2] = n2; }
+    if (vertex_out) {
+        vertex_out[3 * pix] = (float)(p.origin[0] + (double)qx * p.s);
+        vertex_out[3 * pix + 1] = (float)(p.origin[1] + (double)qy * p.s);
+        vertex_out[3 * pix + 2] = (float)(p.origin[2] + (double)qz * p.s);
+    }
+}
+
+template <int kS>
+__global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
     const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
     const unsigned int* __restrict__ occ3, float* __restrict__ depth_out, float* __restrict__ normal_out,
     float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
+    // bracket queue of each warp: pix, z1, f1, z2, f2, dq (x, y, z)
+    __shared__ float sq[kRcWarps][8][kQueue];
+    float(*q)[kQueue] = sq[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const float nanf_ = __int_as_float(0x7fc00000);
     const float h = 0.5f * p.delta;
-    const float eps = 0.02f * (float)p.s;
     const int tiles_x = (p.width + 7) / 8;
     const unsigned n_rays = (unsigned)(tiles_x * ((p.height + 3) / 4)) * 32u;
     const int rtiles_x = (p.width + kRangeTile - 1) / kRangeTile;
     unsigned hits = 0;
+    int queued = 0;     // warp-uniform
 
-    int phase = kPhaseIdle, pix = 0, it = 0, j = 0, side = 0, r = 0, k = 0;
+    // per-lane ray: 0 idle, 1 march, 2 re-scan of the last step
+    int phase = 0, pix = 0, it = 0, j = 0;
     float dqx = 0.f, dqy = 0.f, dqz = 0.f, inv[3] = {0.f, 0.f, 0.f};
     float z = 0.f, zend = 0.f, fprev = 0.f, zprev = 0.f, zprev_any = 0.f, zstep = 0.f;
-    float back = 0.f, fl = 0.f, zl = 0.f, zt = 0.f, ft = 0.f;
-    float z1 = 0.f, f1 = 0.f, z2 = 0.f, f2 = 0.f, zs = 0.f;
-    float qh[3] = {0.f, 0.f, 0.f}, gp = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    float back = 0.f, fl = 0.f, zl = 0.f, ft = 0.f;
     bool prev_def = false, ldef = false, rays_left = true;
-
-    auto write_miss = [&](int px) {
-        if (depth_out) depth_out[px] = 0.0f;
-        if (normal_out) { normal_out[3 * px] = nanf_; normal_out[3 * px + 1] = nanf_; normal_out[3 * px + 2] = nanf_; }
-        if (vertex_out) { vertex_out[3 * px] = nanf_; vertex_out[3 * px + 1] = nanf_; vertex_out[3 * px + 2] = nanf_; }
-    };
 
     for (;;) {
         // hand out rays to idle lanes; a lane keeps drawing until it holds a ray to march
         for (;;) {
-            const bool need = phase == kPhaseIdle && rays_left;
+            const bool need = phase == 0 && rays_left;
             const unsigned msk = __ballot_sync(0xffffffffu, need);
             if (!msk) break;
             unsigned base = 0;
             if (lane == __ffs(msk) - 1) base = atomicAdd(&ctr->rc_next, (unsigned)__popc(msk));
             base = __shfl_sync(0xffffffffu, base, __ffs(msk) - 1);
             if (!need) continue;
-            const unsigned idx = base + (unsigned)__popc(msk & ((1u << lane) - 1u));
+            const unsigned idx = base + (unsigned)__popc(msk & lt_mask);
             if (idx >= n_rays) {
                 rays_left = false;
                 continue;
@@ -465,7 +525,9 @@ __global__ void __launch_bounds__(128) raycast_persistent_kernel(
             z = fmaxf(zn, p.near_clip);
             zend = fminf(zf, p.far_clip);
             if (!(zn <= zf) || !(z <= zend)) {
-                write_miss(pix);
+                if (depth_out) depth_out[pix] = 0.0f;
+                if (normal_out) { normal_out[3 * pix] = nanf_; normal_out[3 * pix + 1] = nanf_; normal_out[3 * pix + 2] = nanf_; }
+                if (vertex_out) { vertex_out[3 * pix] = nanf_; vertex_out[3 * pix + 1] = nanf_; vertex_out[3 * pix + 2] = nanf_; }
                 continue;
             }
             const float dcx = ((float)u - p.cx) / p.fx, dcy = ((float)v - p.cy) / p.fy;
@@ -480,35 +542,35 @@ __global__ void __launch_bounds__(128) raycast_persistent_kernel(
             zprev_any = z;
             zstep = h;
             it = 0;
-            phase = kPhaseMarch;
+            phase = 1;
         }
-        if (!__any_sync(0xffffffffu, phase != kPhaseIdle)) break;
-
-        // one sample per lane
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        bool take = phase != kPhaseIdle;
-        if (phase == kPhaseNormal) {
-            sx = qh[0] + (k == 0 ? 1.0f : k == 1 ? -1.0f : 0.0f);
-            sy = qh[1] + (k == 2 ? 1.0f : k == 3 ? -1.0f : 0.0f);
-            sz = qh[2] + (k == 4 ? 1.0f : k == 5 ? -1.0f : 0.0f);
-        } else {
-            float zq = z;
-            if (phase == kPhaseRescan) {
-                zq = zt - back + (float)j * (back / (float)kFine);
-                take = j < kFine;
-            } else if (phase == kPhaseRefine) {
-                zq = zs;
+        const bool marching = __any_sync(0xffffffffu, phase != 0);
+        if (!marching && queued == 0) break;
+        if (queued >= 32 || !marching) {
+            // the warp refines and shades the newest min(queued, 32) brackets
+            const int n = min(queued, 32);
+            queued -= n;
+            if (lane < n) {
+                const int e = queued + lane;
+                refine_and_shade<kS>(p, table, T, __float_as_int(q[0][e]), q[1][e], q[2][e], q[3][e], q[4][e],
+                                     q[5][e], q[6][e], q[7][e], depth_out, normal_out, vertex_out);
+                ++hits;
             }
-            sx = __fmaf_rn(zq, dqx, p.q0[0]);
-            sy = __fmaf_rn(zq, dqy, p.q0[1]);
-            sz = __fmaf_rn(zq, dqz, p.q0[2]);
+            __syncwarp();
+            continue;
         }
+
+        // one march (or re-scan) sample per busy lane
+        const float zq = phase == 2 && j < kFine ? zt_minus(z, back, j) : z;
         float f = 0.0f;
         int blk[3] = {0, 0, 0};
-        const int st = take ? trilinear<kS>(p, table, T, sx, sy, sz, &f, blk) : 0;
-
-        bool finish = false, found_hit = false, enter_refine = false;
-        if (phase == kPhaseMarch) {
+        const bool take = phase == 1 || (phase == 2 && j < kFine);
+        const int st = take ? trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]), __fmaf_rn(zq, dqy, p.q0[1]),
+                                            __fmaf_rn(zq, dqz, p.q0[2]), &f, blk)
+                            : 0;
+        bool miss = false, push = false;
+        float b1 = 0.f, c1 = 0.f, b2 = 0.f, c2 = 0.f;   // bracket (z1, f1, z2, f2)
+        if (phase == 1) {
             bool done = false;
             if (st == 2) {
                 zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
@@ -518,20 +580,19 @@ __global__ void __launch_bounds__(128) raycast_persistent_kernel(
             } else {
                 const bool def = st == 0;
                 if (def && !prev_def && f <= 0.0f && it > 0) {
-                    // re-scan the last step in the coming iterations
-                    phase = kPhaseRescan;
+                    // re-scan the last step in the coming iterations (z and f kept)
+                    phase = 2;
                     back = fminf(zstep, z - zprev_any);
-                    zt = z;
                     ft = f;
                     j = 0;
                     ldef = false;
                     done = true;
                 } else if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
-                    z1 = zprev; f1 = fprev; z2 = z; f2 = f;
-                    enter_refine = true;
+                    b1 = zprev; c1 = fprev; b2 = z; c2 = f;
+                    push = true;
                     done = true;
                 } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
-                    finish = true;                        // back face first: miss
+                    miss = true;                          // back face first
                     done = true;
                 } else {
                     prev_def = def;
@@ -544,21 +605,20 @@ __global__ void __launch_bounds__(128) raycast_persistent_kernel(
             }
             if (!done) {
                 ++it;
-                if (!(it < kMaxMarch && z <= zend)) finish = true;
+                if (!(it < kMaxMarch && z <= zend)) miss = true;
             }
-        } else if (phase == kPhaseRescan) {
-            const float zq = j == kFine ? zt : zt - back + (float)j * (back / (float)kFine);
+        } else if (phase == 2) {
             const float fq = j == kFine ? ft : f;
-            const int sq = j == kFine ? 0 : st;
+            const int sq_ = j == kFine ? 0 : st;
             bool resolved = false;
-            if (sq != 0) {
+            if (sq_ != 0) {
                 ldef = false;
             } else if (ldef && fl > 0.0f && fq <= 0.0f) {
-                z1 = zl; f1 = fl; z2 = zq; f2 = fq;
-                enter_refine = true;
+                b1 = zl; c1 = fl; b2 = zq; c2 = fq;
+                push = true;
                 resolved = true;
             } else if (ldef && fl < 0.0f && fq > 0.0f) {
-                finish = true;
+                miss = true;
                 resolved = true;
             } else {
                 ldef = true; fl = fq; zl = zq;
@@ -567,95 +627,30 @@ __global__ void __launch_bounds__(128) raycast_persistent_kernel(
                 // nothing found: continue the march after the re-scanned sample
                 prev_def = true;
                 fprev = ft;
-                zprev = zt;
-                zprev_any = zt;
+                zprev = z;
+                zprev_any = z;
                 zstep = h;
-                z = zt + h;
-                phase = kPhaseMarch;
+                z += h;
+                phase = 1;
                 ++it;
-                if (!(it < kMaxMarch && z <= zend)) finish = true;
-            }
-        } else if (phase == kPhaseRefine) {
-            // the sample at zs was taken this iteration (refinement step r)
-            if (st != 0) {
-                phase = kPhaseNormal;
-            } else {
-                if (f > 0.0f) {
-                    z1 = zs; f1 = f;
-                    if (side == 1) f2 *= 0.5f;
-                    side = 1;
-                } else {
-                    z2 = zs; f2 = f;
-                    if (side == -1) f1 *= 0.5f;
-                    side = -1;
-                }
-                ++r;
-                if (f1 == f2) {
-                    phase = kPhaseNormal;
-                } else {
-                    zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
-                    if (!(r < kRefine && z2 - z1 > eps)) phase = kPhaseNormal;
-                }
-            }
-            if (phase == kPhaseNormal) {
-                qh[0] = __fmaf_rn(zs, dqx, p.q0[0]);
-                qh[1] = __fmaf_rn(zs, dqy, p.q0[1]);
-                qh[2] = __fmaf_rn(zs, dqz, p.q0[2]);
-                k = 0;
-            }
-        } else if (phase == kPhaseNormal) {
-            if (st != 0) {
-                found_hit = true;                         // hit with an undefined gradient
-                g0 = g1 = g2 = nanf_;
-                finish = true;
-            } else {
-                if ((k & 1) == 0) gp = f;
-                else if (k == 1) g0 = gp - f;
-                else if (k == 3) g1 = gp - f;
-                else g2 = gp - f;
-                if (++k == 6) {
-                    found_hit = true;
-                    finish = true;
-                }
+                if (!(it < kMaxMarch && z <= zend)) miss = true;
             }
         }
-        if (enter_refine) {
-            // Illinois false position on [z1, z2]: first secant estimate; a
-            // bracket already narrower than eps goes straight to the normal
-            side = 0;
-            r = 0;
-            zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
-            phase = z2 - z1 > eps ? kPhaseRefine : kPhaseNormal;
-            if (phase == kPhaseNormal) {
-                qh[0] = __fmaf_rn(zs, dqx, p.q0[0]);
-                qh[1] = __fmaf_rn(zs, dqy, p.q0[1]);
-                qh[2] = __fmaf_rn(zs, dqz, p.q0[2]);
-                k = 0;
-            }
+        const unsigned pm = __ballot_sync(0xffffffffu, push);
+        if (push) {
+            const int e = queued + __popc(pm & lt_mask);
+            q[0][e] = __int_as_float(pix);
+            q[1][e] = b1; q[2][e] = c1; q[3][e] = b2; q[4][e] = c2;
+            q[5][e] = dqx; q[6][e] = dqy; q[7][e] = dqz;
+            phase = 0;
         }
-        if (finish) {
-            if (found_hit) {
-                float n0 = nanf_, n1 = nanf_, n2 = nanf_;
-                if (!isnan(g0)) {
-                    const float gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-                    if (gn > 0.0f) {
-                        const float sg = (g0 * dqx + g1 * dqy + g2 * dqz) > 0.0f ? -1.0f : 1.0f;
-                        const float iv = sg / gn;
-                        n0 = g0 * iv; n1 = g1 * iv; n2 = g2 * iv;
-                    }
-                }
-                if (depth_out) depth_out[pix] = zs;
-                if (normal_out) { normal_out[3 * pix] = n0; normal_out[3 * pix + 1] = n1; normal_out[3 * pix + 2] = n2; }
-                if (vertex_out) {
-                    vertex_out[3 * pix] = (float)(p.origin[0] + (double)qh[0] * p.s);
-                    vertex_out[3 * pix + 1] = (float)(p.origin[1] + (double)qh[1] * p.s);
-                    vertex_out[3 * pix + 2] = (float)(p.origin[2] + (double)qh[2] * p.s);
-                }
-                ++hits;
-            } else {
-                write_miss(pix);
-            }
-            phase = kPhaseIdle;
+        queued += __popc(pm);
+        __syncwarp();
+        if (miss) {
+            if (depth_out) depth_out[pix] = 0.0f;
+            if (normal_out) { normal_out[3 * pix] = nanf_; normal_out[3 * pix + 1] = nanf_; normal_out[3 * pix + 2] = nanf_; }
+            if (vertex_out) { vertex_out[3 * pix] = nanf_; vertex_out[3 * pix + 1] = nanf_; vertex_out[3 * pix + 2] = nanf_; }
+            phase = 0;
         }
     }
     hits = warp_sum(hits);
@@ -688,11 +683,11 @@ void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
         // exactly the CTAs that fit at once: a CTA launched later would find no rays left
         static int per_sm = 0;
         if (per_sm == 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_persistent_kernel<kS>, 128, 0) !=
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_persistent_kernel<kS>, 32 * kRcWarps, 0) !=
                  cudaSuccess ||
              per_sm < 1))
             per_sm = 1;
-        raycast_persistent_kernel<kS><<<v->num_sms * per_sm, 128, 0, st>>>(
+        raycast_persistent_kernel<kS><<<v->num_sms * per_sm, 32 * kRcWarps, 0, st>>>(
             p, near_, far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
             normal_out, vertex_out, v->ctr);
         return;
