@@ -69,6 +69,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(seconds: float, world: int, device="cpu") -> float:
+    """The slowest rank's time: every rank gets the all-reduce MAX of its own."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,12 +309,9 @@ def run_ours(args):
             stage += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
     stage_ms_per_step = stage / args.steps
 
-    t_max = torch.tensor([elapsed], device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t_max.item())
+    elapsed_max = max_over_ranks(elapsed, world, dev)
     frames_total = F * args.steps * world
-    value = frames_total / elapsed_max
+    value = job_throughput(F * args.steps, world, elapsed_max)
     updates_per_step = st["voxel_updates_total"]
     rays_per_step = F * H * W
 
@@ -371,10 +384,8 @@ def run_ours(args):
             vol.stats()     # synchronises and reads the step's counters
         torch.cuda.synchronize()
         e2e_sec = time.perf_counter() - w0
-        te = torch.tensor([e2e_sec], device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": frames_total / float(te.item()), "unit": UNIT,
+        line["e2e"] = {"value": job_throughput(F * args.steps, world, max_over_ranks(e2e_sec, world, dev)),
+                       "unit": UNIT,
                        "h2d_bytes_per_step": int(F * H * W * 4),
                        "d2h_bytes_per_step": int(28 * H * W + 11 * 8)}
 
@@ -537,6 +548,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "room" and dist_env()[2] > 1:
+        raise SystemExit(f"--workload {args.workload} is a single-GPU measurement; run it without torchrun")
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "capsules":
