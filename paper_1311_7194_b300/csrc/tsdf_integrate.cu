@@ -250,6 +250,9 @@ __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock
     if (!(uf >= 0.0f && uf < (float)p.width && vf >= 0.0f && vf < (float)p.height)) return false;
     const int pix = (int)floorf(vf) * p.width + (int)floorf(uf);
     const float D = __ldg(depth + pix);
+    // the band test first: most voxels that get here fail it
+    const float t = __fsub_rn(__fsub_rn(D, vb.o[2]), zs);
+    if (!(fabsf(t) <= p.delta)) return false;
     if (!depth_ok(D, p.depth_min, p.depth_max)) return false;
     float pv;
     if (kVarMap) {
@@ -259,8 +262,6 @@ __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock
         pv = __fmul_rn(sg, sg);
     }
     if (!(pv > 0.0f && pv <= 3.0e38f)) return false;
-    const float t = __fsub_rn(__fsub_rn(D, vb.o[2]), zs);
-    if (!(fabsf(t) <= p.delta)) return false;
     *Tk = t;
     *pk = pv;
     return true;

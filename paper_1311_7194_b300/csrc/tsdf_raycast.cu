@@ -494,17 +494,19 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     unsigned hits = 0;
     int queued = 0;     // warp-uniform
 
-    // per-lane ray: 0 idle, 1 march, 2 re-scan of the last step
-    int phase = 0, pix = 0, it = 0, j = 0;
-    float dqx = 0.f, dqy = 0.f, dqz = 0.f, inv[3] = {0.f, 0.f, 0.f};
-    float z = 0.f, zend = 0.f, fprev = 0.f, zprev = 0.f, zprev_any = 0.f, zstep = 0.f;
-    float back = 0.f, fl = 0.f, zl = 0.f, ft = 0.f;
-    bool prev_def = false, ldef = false, rays_left = true;
+    // The march state of a lane's ray, kept small (the kernel is latency-bound
+    // and registers decide how many warps an SM holds): zl is the camera z of
+    // the last sample taken (the bracket's near end when that sample was
+    // defined), zstep the step since; the re-scan runs inline.
+    bool busy = false, prev_def = false, rays_left = true;
+    int pix = 0, it = 0;
+    float dqx = 0.f, dqy = 0.f, dqz = 0.f;
+    float z = 0.f, zend = 0.f, fprev = 0.f, zl = 0.f, zstep = 0.f;
 
     for (;;) {
         // hand out rays to idle lanes; a lane keeps drawing until it holds a ray to march
         for (;;) {
-            const bool need = phase == 0 && rays_left;
+            const bool need = !busy && rays_left;
             const unsigned msk = __ballot_sync(0xffffffffu, need);
             if (!msk) break;
             unsigned base = 0;
@@ -534,17 +536,14 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             dqx = p.Rs[0] * dcx + p.Rs[1] * dcy + p.Rs[2];
             dqy = p.Rs[3] * dcx + p.Rs[4] * dcy + p.Rs[5];
             dqz = p.Rs[6] * dcx + p.Rs[7] * dcy + p.Rs[8];
-            inv[0] = dqx != 0.0f ? 1.0f / dqx : 0.0f;
-            inv[1] = dqy != 0.0f ? 1.0f / dqy : 0.0f;
-            inv[2] = dqz != 0.0f ? 1.0f / dqz : 0.0f;
             prev_def = false;
-            fprev = zprev = 0.0f;
-            zprev_any = z;
+            fprev = 0.0f;
+            zl = z;
             zstep = h;
             it = 0;
-            phase = 1;
+            busy = true;
         }
-        const bool marching = __any_sync(0xffffffffu, phase != 0);
+        const bool marching = __any_sync(0xffffffffu, busy);
         if (!marching && queued == 0) break;
         if (queued >= 32 || !marching) {
             // the warp refines and shades the newest min(queued, 32) brackets
@@ -560,78 +559,70 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             continue;
         }
 
-        // one march (or re-scan) sample per busy lane
-        const float zq = phase == 2 && j < kFine ? zt_minus(z, back, j) : z;
+        // one march sample per busy lane
         float f = 0.0f;
         int blk[3] = {0, 0, 0};
-        const bool take = phase == 1 || (phase == 2 && j < kFine);
-        const int st = take ? trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]), __fmaf_rn(zq, dqy, p.q0[1]),
-                                            __fmaf_rn(zq, dqz, p.q0[2]), &f, blk)
+        const int st = busy ? trilinear<kS>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
+                                            __fmaf_rn(z, dqz, p.q0[2]), &f, blk)
                             : 0;
         bool miss = false, push = false;
         float b1 = 0.f, c1 = 0.f, b2 = 0.f, c2 = 0.f;   // bracket (z1, f1, z2, f2)
-        if (phase == 1) {
+        if (busy) {
             bool done = false;
             if (st == 2) {
-                zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
-                z = zprev_any + 1e-3f * h;
-                zstep = z - zprev_any;
+                const float inv[3] = {dqx != 0.0f ? 1.0f / dqx : 0.0f, dqy != 0.0f ? 1.0f / dqy : 0.0f,
+                                      dqz != 0.0f ? 1.0f / dqz : 0.0f};
+                zl = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
+                z = zl + 1e-3f * h;
+                zstep = z - zl;
                 prev_def = false;
             } else {
                 const bool def = st == 0;
                 if (def && !prev_def && f <= 0.0f && it > 0) {
-                    // re-scan the last step in the coming iterations (z and f kept)
-                    phase = 2;
-                    back = fminf(zstep, z - zprev_any);
-                    ft = f;
-                    j = 0;
-                    ldef = false;
-                    done = true;
-                } else if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
-                    b1 = zprev; c1 = fprev; b2 = z; c2 = f;
-                    push = true;
-                    done = true;
-                } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
-                    miss = true;                          // back face first
-                    done = true;
-                } else {
-                    prev_def = def;
-                    fprev = f;
-                    zprev = z;
-                    zprev_any = z;
-                    zstep = def ? h : 2.0f * h;
-                    z += zstep;
+                    // The field starts here already at or below zero: re-scan
+                    // the last step in kFine substeps for a short positive run.
+                    bool ldef = false;
+                    float fa = 0.0f, za = 0.0f;
+                    const float back = fminf(zstep, z - zl);
+                    for (int j = 0; j <= kFine && !done; ++j) {
+                        const float zq = j == kFine ? z : zt_minus(z, back, j);
+                        float fq = f;
+                        const int sq_ = j == kFine ? 0
+                                                   : trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
+                                                                   __fmaf_rn(zq, dqy, p.q0[1]),
+                                                                   __fmaf_rn(zq, dqz, p.q0[2]), &fq, blk);
+                        if (sq_ != 0) {
+                            ldef = false;
+                        } else if (ldef && fa > 0.0f && fq <= 0.0f) {
+                            b1 = za; c1 = fa; b2 = zq; c2 = fq;
+                            push = true;
+                            done = true;
+                        } else if (ldef && fa < 0.0f && fq > 0.0f) {
+                            miss = true;
+                            done = true;
+                        } else {
+                            ldef = true; fa = fq; za = zq;
+                        }
+                    }
+                }
+                if (!done) {
+                    if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
+                        b1 = zl; c1 = fprev; b2 = z; c2 = f;
+                        push = true;
+                        done = true;
+                    } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
+                        miss = true;                      // back face first
+                        done = true;
+                    } else {
+                        prev_def = def;
+                        fprev = f;
+                        zl = z;
+                        zstep = def ? h : 2.0f * h;
+                        z += zstep;
+                    }
                 }
             }
             if (!done) {
-                ++it;
-                if (!(it < kMaxMarch && z <= zend)) miss = true;
-            }
-        } else if (phase == 2) {
-            const float fq = j == kFine ? ft : f;
-            const int sq_ = j == kFine ? 0 : st;
-            bool resolved = false;
-            if (sq_ != 0) {
-                ldef = false;
-            } else if (ldef && fl > 0.0f && fq <= 0.0f) {
-                b1 = zl; c1 = fl; b2 = zq; c2 = fq;
-                push = true;
-                resolved = true;
-            } else if (ldef && fl < 0.0f && fq > 0.0f) {
-                miss = true;
-                resolved = true;
-            } else {
-                ldef = true; fl = fq; zl = zq;
-            }
-            if (!resolved && ++j > kFine) {
-                // nothing found: continue the march after the re-scanned sample
-                prev_def = true;
-                fprev = ft;
-                zprev = z;
-                zprev_any = z;
-                zstep = h;
-                z += h;
-                phase = 1;
                 ++it;
                 if (!(it < kMaxMarch && z <= zend)) miss = true;
             }
@@ -642,7 +633,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             q[0][e] = __int_as_float(pix);
             q[1][e] = b1; q[2][e] = c1; q[3][e] = b2; q[4][e] = c2;
             q[5][e] = dqx; q[6][e] = dqy; q[7][e] = dqz;
-            phase = 0;
+            busy = false;
         }
         queued += __popc(pm);
         __syncwarp();
@@ -650,7 +641,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             if (depth_out) depth_out[pix] = 0.0f;
             if (normal_out) { normal_out[3 * pix] = nanf_; normal_out[3 * pix + 1] = nanf_; normal_out[3 * pix + 2] = nanf_; }
             if (vertex_out) { vertex_out[3 * pix] = nanf_; vertex_out[3 * pix + 1] = nanf_; vertex_out[3 * pix + 2] = nanf_; }
-            phase = 0;
+            busy = false;
         }
     }
     hits = warp_sum(hits);
