@@ -218,11 +218,40 @@ def _sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-# DRAM traffic of the integrate stage measured by ncu on this workload, per
-# voxel update (dram__bytes_read.sum + dram__bytes_write.sum over the stage's
-# kernels / voxel updates), with the source hash it was measured on; the value is
-# dropped when the kernel source changes.
-NCU_TRAFFIC = {"integrate": None}
+# DRAM traffic of a stage measured by ncu on this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum over the stage's kernels), per
+# voxel update for the integrate stage and per traced unique byte for the
+# raycast stage,
+# with the hash of the kernel source it was measured on; a value is dropped
+# when that source changes.
+NCU_TRAFFIC = {
+    # frames 100-109, 10 launches each of depth_tiles + cull + integrate + reset:
+    # 2098.2 MB over 76.55 M voxel updates
+    "integrate": {"sha": "05265be1a6d77b34", "bytes_per_unit": 27.41},
+    # same frames, 10 launches each of reset + clear + range cull + raster +
+    # persistent raycast: 1015.2 MB against 816.0 MB of traced unique bytes,
+    # i.e. DRAM bytes per algorithmic byte
+    "raycast": {"sha": "d5f52604ae415e3a", "bytes_per_unit": 1.2441},
+}
+STAGE_SOURCES = {"integrate": "tsdf_integrate.cu", "raycast": "tsdf_raycast.cu"}
+TRACE_EVERY = 10
+
+
+def ncu_traffic(stage, units):
+    rec = NCU_TRAFFIC.get(stage)
+    src = os.path.join(ROOT, "paper_1311_7194_b300", "csrc", STAGE_SOURCES[stage])
+    if not rec or rec.get("sha") != _sha(src):
+        return None
+    return rec["bytes_per_unit"] * units
+
+
+def raycast_algorithmic_bytes(counts, n_blocks, H, W):
+    """Unique bytes one raycast must move: the distinct 32-byte sectors of T
+    and of the block table its samples read, the block list read by the range
+    cull (16 B per block), the near / far range tiles (8 B per 4x4 pixels) and
+    the depth, normal and vertex maps written (28 B per pixel)."""
+    tiles = ((W + 3) // 4) * ((H + 3) // 4)
+    return 32.0 * (counts["t_sectors"] + counts["table_sectors"]) + 16.0 * n_blocks + 8.0 * tiles + 28.0 * H * W
 
 
 def run_ours(args):
@@ -315,32 +344,43 @@ def run_ours(args):
     updates_per_step = st["voxel_updates_total"]
     rays_per_step = F * H * W
 
-    # per-frame work counts (one extra, untimed step, synchronising per frame)
+    # per-frame work counts (one extra, untimed step, synchronising per frame);
+    # every TRACE_EVERY-th frame's raycast is traced for its unique bytes
     vol.reset()
-    n_blocks, visible, updates = [], [], []
+    n_blocks, visible, updates, rc_bytes = [], [], [], []
     for k in range(F):
         vol.allocate(depth_dev[k], seq.intr, seq.poses[k])
         vol.integrate(depth_dev[k], seq.intr, seq.poses[k])
         s_ = vol.stats()
         n_blocks.append(s_["n_blocks"]); visible.append(s_["visible_blocks"]); updates.append(s_["voxel_updates"])
+        if k % TRACE_EVERY == 0:
+            c = vol.raycast_trace(seq.intr, seq.poses[k])
+            rc_bytes.append(raycast_algorithmic_bytes(c, s_["n_blocks"], H, W))
     n_blocks, visible, updates = map(np.asarray, (n_blocks, visible, updates))
+    peak, peak_kind = peaks()
     # integrate stage, algorithmic bytes per frame: read+write T and P of every
     # updated voxel (16 B), the depth map (4 B/px), the block list read by the
     # cull (16 B/block) and the visible list written and read (32 B each way)
     integ_bytes = 16.0 * updates + 4.0 * H * W + 16.0 * n_blocks + 64.0 * visible
     integ_sec = stage_ms_per_step[1] / 1000.0
-    peak, peak_kind = peaks()
     achieved = integ_bytes.sum() / integ_sec / 1e9
-    integ_src = os.path.join(ROOT, "paper_1311_7194_b300", "csrc", "tsdf_integrate.cu")
-    traffic = None
-    rec = NCU_TRAFFIC.get("integrate")
-    if rec and rec.get("sha") == _sha(integ_src):
-        traffic = rec["bytes_per_update"] * float(updates.mean())
-    roofline = {"kernel": "integrate stage (cull + Alg. 3 integrate), per frame", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": peak_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": float(integ_bytes.mean()),
-                "avg_launch_ms": 1000.0 * integ_sec / F}
+    roofline_integrate = {"kernel": "integrate stage (depth tiles + cull + Alg. 3 integrate), per frame",
+                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "peak_kind": peak_kind,
+                          "traffic": ncu_traffic("integrate", float(updates.mean())),
+                          "algorithmic_bytes_per_launch": float(integ_bytes.mean()),
+                          "avg_launch_ms": 1000.0 * integ_sec / F}
+    # raycast stage (the dominant one): unique bytes it must read and write
+    rc_mean = float(np.mean(rc_bytes))
+    rc_sec = stage_ms_per_step[2] / 1000.0 / F
+    roofline = {"kernel": "raycast stage (range cull + raster + persistent march / refine / normal), per frame",
+                "bound": "hbm", "achieved": rc_mean / rc_sec / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": rc_mean / rc_sec / 1e9 / peak, "peak_kind": peak_kind,
+                "traffic": ncu_traffic("raycast", rc_mean), "algorithmic_bytes_per_launch": rc_mean,
+                "avg_launch_ms": 1000.0 * rc_sec,
+                "algorithmic_bytes": "distinct 32 B sectors of T and of the block table read (traced every "
+                                     f"{TRACE_EVERY}th frame) + 16 B per allocated block (range cull) + "
+                                     "8 B per 4x4-pixel range tile + 28 B per pixel of maps written"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed_max / args.steps, "higher_is_better": True,
@@ -359,7 +399,7 @@ def run_ours(args):
             "work_per_step": {"voxel_updates": int(updates_per_step), "blocks": int(st["n_blocks"]),
                               "visible_blocks": int(st["visible_blocks_total"]),
                               "rays_hit": int(st["rays_hit_total"])},
-            "roofline": roofline,
+            "roofline": roofline, "roofline_integrate": roofline_integrate,
             "gpu_launches": LAUNCHES_PER_FRAME * F * args.steps,
             "clocks": clk}
 

@@ -222,6 +222,28 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const doubl
 tsdf_status tsdf_raycast_noalloc(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
                                  float* depth_out, float* normal_out, float* vertex_out, void* stream);
 
+/* Traversal counts of one raycast, for measurement (no counterpart in the
+ * paper). */
+typedef struct {
+    int64_t samples;        /* trilinear samples taken (march, re-scan, refinement, normal) */
+    int64_t table_lookups;  /* block-table entries read by those samples */
+    int64_t t_sectors;      /* distinct 32-byte sectors of the T pool read */
+    int64_t table_sectors;  /* distinct 32-byte sectors of the block table read */
+    int64_t rays;           /* W * H */
+    int64_t rays_hit;
+} tsdf_raycast_counts;
+
+/* Run the raycast of tsdf_raycast at pose_wc with every sample traced and
+ * return the counts in *out (host struct). Same rays, samples and crossings as
+ * tsdf_raycast (the one-thread-per-pixel kernel with tracing compiled in); no
+ * maps are written. It gives the unique bytes a raycast must read, the
+ * algorithmic bytes of the raycast's roofline. Slow and synchronous: it
+ * allocates and frees one flag byte per 32 bytes of the T pool and of the block
+ * table (e.g. 64 + 8 MiB for 2^20 float32 blocks on a 2048^3 grid). Counts as a
+ * raycast in tsdf_get_stats. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_raycast_trace(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
+                               tsdf_raycast_counts* out, void* stream);
+
 /* CUDA-graph driver of the per-step pipeline (no counterpart in the paper; it
  * removes per-kernel launch gaps). A step fuses K frames (1 <= K <= 8) exactly
  * as tsdf_integrate (K = 1) or tsdf_integrate_batch (K > 1) would, then

@@ -159,6 +159,9 @@ cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameP
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
 // Raycast with caller-provided near / far range maps (each W*H words).
+cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned char* t_sector, long long n_t,
+                                 unsigned char* table_sector, long long n_table, unsigned long long* counts,
+                                 cudaStream_t st);
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st);
 cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out,

@@ -163,6 +163,30 @@ __device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__
     return slot < 0 ? __int_as_float(0x7fc00000) : Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, sc);
 }
 
+// Traversal tracing (tsdf_raycast_trace only; compiled out of every other
+// kernel): samples, block-table lookups, and flags for each 32-byte sector of
+// T and of the block table that a sample reads.
+struct TraceState {
+    unsigned char* t_sector;       // one flag per 32 B of the T pool
+    unsigned char* table_sector;   // one flag per 32 B of the block table
+    unsigned long long* counts;    // [0] samples, [1] table lookups
+    int t_bytes;                   // bytes per stored T value
+};
+__device__ TraceState g_trace;
+
+template <int kS>
+__device__ __forceinline__ void trace_corner(int slot, int off) {
+    if (slot < 0) return;
+    const unsigned long long byte = ((unsigned long long)slot * kBlockVoxels + (unsigned)off) * (unsigned)g_trace.t_bytes;
+    g_trace.t_sector[byte >> 5] = 1;
+}
+
+__device__ __forceinline__ void trace_lookup(const FrameParams& p, int bx, int by, int bz) {
+    const unsigned long long e = (unsigned)bx + (unsigned long long)p.nb * ((unsigned)by + (unsigned long long)p.nb * (unsigned)bz);
+    g_trace.table_sector[e >> 3] = 1;
+    atomicAdd(&g_trace.counts[1], 1ull);
+}
+
 // Trilinear T at voxel-space point q. Returns 0 = defined (value in *f),
 // 1 = undefined (a corner is chi, unallocated or outside the grid),
 // 2 = the lower corner's block is unallocated or outside the grid (the caller
@@ -170,10 +194,11 @@ __device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__
 // The 8 corners are fetched by the same instructions whether or not the cell
 // crosses a block face (only the extra block lookups are conditional), which
 // keeps the lanes of a warp together.
-template <int kS>
+template <int kS, bool kTrace = false>
 __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __restrict__ table,
                                          const typename Codec<kS>::E* __restrict__ T, float qx, float qy, float qz,
                                          float* f, int* blk) {
+    if (kTrace) atomicAdd(&g_trace.counts[0], 1ull);
     const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
     const int ix = (int)fmaxf(fminf(fx0, 1e9f), -1e9f);
     const int iy = (int)fmaxf(fminf(fy0, 1e9f), -1e9f);
@@ -182,24 +207,44 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
     blk[0] = bx; blk[1] = by; blk[2] = bz;
     if (bx < 0 || by < 0 || bz < 0 || bx >= p.nb || by >= p.nb || bz >= p.nb) return 2;
     const int s000 = slot_of(p, table, bx, by, bz);
+    if (kTrace) trace_lookup(p, bx, by, bz);
     if (s000 < 0) return 2;
     if (ix + 1 >= p.G || iy + 1 >= p.G || iz + 1 >= p.G) return 1;
     const int lx = ix & 7, ly = iy & 7, lz = iz & 7;
     const int ex = lx == 7, ey = ly == 7, ez = lz == 7;
+    // Corner (dx, dy, dz) lies in block (bx + ex dx, by + ey dy, bz + ez dz):
+    // each distinct block is looked up once (a cell crossing one face needs
+    // one more block, two faces three more, three faces seven more).
     int s100 = s000, s010 = s000, s110 = s000, s001 = s000, s101 = s000, s011 = s000, s111 = s000;
     if (ex | ey | ez) {   // corners in up to 8 blocks
         if (ex) s100 = slot_of(p, table, bx + 1, by, bz);
         if (ey) s010 = slot_of(p, table, bx, by + 1, bz);
-        if (ex | ey) s110 = slot_of(p, table, bx + ex, by + ey, bz);
         if (ez) s001 = slot_of(p, table, bx, by, bz + 1);
-        if (ex | ez) s101 = slot_of(p, table, bx + ex, by, bz + ez);
-        if (ey | ez) s011 = slot_of(p, table, bx, by + ey, bz + ez);
-        s111 = slot_of(p, table, bx + ex, by + ey, bz + ez);
+        s110 = (ex & ey) ? slot_of(p, table, bx + 1, by + 1, bz) : (ex ? s100 : s010);
+        s101 = (ex & ez) ? slot_of(p, table, bx + 1, by, bz + 1) : (ex ? s100 : s001);
+        s011 = (ey & ez) ? slot_of(p, table, bx, by + 1, bz + 1) : (ey ? s010 : s001);
+        s111 = (ex & ey & ez) ? slot_of(p, table, bx + 1, by + 1, bz + 1) : (ex & ey) ? s110 : (ex & ez) ? s101
+               : (ey & ez) ? s011 : ex ? s100 : ey ? s010 : s001;
+        if (kTrace) {
+            if (ex) trace_lookup(p, bx + 1, by, bz);
+            if (ey) trace_lookup(p, bx, by + 1, bz);
+            if (ez) trace_lookup(p, bx, by, bz + 1);
+            if (ex & ey) trace_lookup(p, bx + 1, by + 1, bz);
+            if (ex & ez) trace_lookup(p, bx + 1, by, bz + 1);
+            if (ey & ez) trace_lookup(p, bx, by + 1, bz + 1);
+            if (ex & ey & ez) trace_lookup(p, bx + 1, by + 1, bz + 1);
+        }
     }
     const int x0 = lx, x1 = ex ? 0 : lx + 1;
     const int y0 = 8 * ly, y1 = ey ? 0 : 8 * (ly + 1);
     const int z0 = 64 * lz, z1 = ez ? 0 : 64 * (lz + 1);
     const float2 sc = p.tsc;
+    if (kTrace) {
+        trace_corner<kS>(s000, x0 + y0 + z0); trace_corner<kS>(s100, x1 + y0 + z0);
+        trace_corner<kS>(s010, x0 + y1 + z0); trace_corner<kS>(s110, x1 + y1 + z0);
+        trace_corner<kS>(s001, x0 + y0 + z1); trace_corner<kS>(s101, x1 + y0 + z1);
+        trace_corner<kS>(s011, x0 + y1 + z1); trace_corner<kS>(s111, x1 + y1 + z1);
+    }
     const float c000 = voxel<kS>(T, s000, x0 + y0 + z0, sc), c100 = voxel<kS>(T, s100, x1 + y0 + z0, sc);
     const float c010 = voxel<kS>(T, s010, x0 + y1 + z0, sc), c110 = voxel<kS>(T, s110, x1 + y1 + z0, sc);
     const float c001 = voxel<kS>(T, s001, x0 + y0 + z1, sc), c101 = voxel<kS>(T, s101, x1 + y0 + z1, sc);
@@ -245,7 +290,7 @@ __device__ __forceinline__ float empty_exit(const FrameParams& p, const unsigned
     return ze;
 }
 
-template <int kS, int kTW, int kTH>
+template <int kS, int kTW, int kTH, bool kTrace = false>
 __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p, const unsigned int* __restrict__ near_,
                                                       const unsigned int* __restrict__ far_,
                                                       const int* __restrict__ table,
@@ -280,7 +325,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
             float zprev_any = z, zstep = h;   // last sample taken and the step since
             int blk[3];
             for (int it = 0; it < kMaxMarch && z <= zend; ++it) {
-                const int st = trilinear<kS>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
+                const int st = trilinear<kS, kTrace>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
                                          __fmaf_rn(z, dqz, p.q0[2]), &f, blk);
                 if (st == 2) {
                     // everything before the empty cell's exit is undefined
@@ -302,7 +347,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                         const float zq = j == kFine ? z : z - back + (float)j * (back / (float)kFine);
                         float fq = f;
                         const int sq = j == kFine ? 0
-                                                  : trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
+                                                  : trilinear<kS, kTrace>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
                                                               __fmaf_rn(zq, dqy, p.q0[1]), __fmaf_rn(zq, dqz, p.q0[2]),
                                                               &fq, blk);
                         if (sq != 0) {
@@ -350,7 +395,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                 zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
                 for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
                     float fs;
-                    if (trilinear<kS>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
+                    if (trilinear<kS, kTrace>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
                                   __fmaf_rn(zs, dqz, p.q0[2]), &fs, blk) != 0)
                         break;
                     if (fs > 0.0f) {
@@ -369,12 +414,12 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                             qz = __fmaf_rn(zs, dqz, p.q0[2]);
                 float fp[3], fm[3];
                 bool ok = true;
-                ok = ok && trilinear<kS>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk) == 0;
-                ok = ok && trilinear<kS>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk) == 0;
-                ok = ok && trilinear<kS>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk) == 0;
-                ok = ok && trilinear<kS>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk) == 0;
-                ok = ok && trilinear<kS>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk) == 0;
-                ok = ok && trilinear<kS>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk) == 0;
+                ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk) == 0;
                 if (ok) {
                     float g[3] = {fp[0] - fm[0], fp[1] - fm[1], fp[2] - fm[2]};
                     const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
@@ -724,6 +769,52 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
     raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    return cudaGetLastError();
+}
+
+namespace {
+
+__global__ void __launch_bounds__(256) count_flags_kernel(const unsigned char* __restrict__ f, long long n,
+                                                          unsigned long long* __restrict__ out) {
+    unsigned c = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += f[i] != 0;
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+template <int kS>
+void launch_march_traced(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
+                         cudaStream_t st) {
+    const dim3 grid((p.width + 15) / 16, (p.height + 7) / 8);
+    raycast_kernel<kS, 16, 8, true><<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot,
+                                                         static_cast<const typename Codec<kS>::E*>(v->T), v->occ2,
+                                                         v->occ3, nullptr, nullptr, nullptr, v->ctr);
+}
+
+}  // namespace
+
+cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned char* t_sector, long long n_t,
+                                 unsigned char* table_sector, long long n_table, unsigned long long* counts,
+                                 cudaStream_t st) {
+    const TraceState ts{t_sector, table_sector, counts, storage_bytes(v->cfg.storage)};
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_trace, &ts, sizeof(ts), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
+                           ((p.height + kRangeTile - 1) / kRangeTile);
+    unsigned int* near_ = v->range;
+    unsigned int* far_ = v->range + v->range_pixels;
+    reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
+    range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
+    rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
+    raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
+    switch (v->cfg.storage) {
+        case TSDF_STORAGE_F16: launch_march_traced<TSDF_STORAGE_F16>(v, p, near_, far_, st); break;
+        case TSDF_STORAGE_SNORM16: launch_march_traced<TSDF_STORAGE_SNORM16>(v, p, near_, far_, st); break;
+        default: launch_march_traced<TSDF_STORAGE_F32>(v, p, near_, far_, st); break;
+    }
+    count_flags_kernel<<<v->num_sms * 4, 256, 0, st>>>(t_sector, n_t, counts + 2);
+    count_flags_kernel<<<v->num_sms * 4, 256, 0, st>>>(table_sector, n_table, counts + 3);
     return cudaGetLastError();
 }
 

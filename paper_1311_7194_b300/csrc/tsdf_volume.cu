@@ -434,6 +434,44 @@ tsdf_status tsdf_raycast(tsdf_volume* v, const tsdf_intrinsics* K, const double 
     return fail_cuda(v, tsdf::launch_raycast(v, p, depth_out, normal_out, vertex_out, st));
 }
 
+tsdf_status tsdf_raycast_trace(tsdf_volume* v, const tsdf_intrinsics* K, const double pose_wc[16],
+                               tsdf_raycast_counts* out, void* stream) {
+    if (!v || !out || !intr_ok(K) || !pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const cudaError_t eb = tsdf::ensure_range(v, *K, st);
+    if (eb != cudaSuccess) return fail_cuda(v, eb);
+    const FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
+    v->last_stream = st;
+    const long long n_t = (long long)((v->cfg.block_capacity * tsdf::kBlockVoxels *
+                                       (int64_t)tsdf::storage_bytes(v->cfg.storage) + 31) / 32);
+    const long long n_table = (long long)((v->n_table + 7) / 8);
+    unsigned char *t_sector = nullptr, *table_sector = nullptr;
+    unsigned long long* counts = nullptr;
+    cudaError_t e = cudaMalloc(&t_sector, (size_t)n_t);
+    if (e == cudaSuccess) e = cudaMalloc(&table_sector, (size_t)n_table);
+    if (e == cudaSuccess) e = cudaMalloc(&counts, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(t_sector, 0, (size_t)n_t, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(table_sector, 0, (size_t)n_table, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = tsdf::launch_raycast_trace(v, p, t_sector, n_t, table_sector, n_table, counts, st);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long hits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c, counts, sizeof(c), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hits, &v->ctr->rays_hit, sizeof(hits), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(t_sector);
+    cudaFree(table_sector);
+    cudaFree(counts);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    out->samples = (int64_t)c[0];
+    out->table_lookups = (int64_t)c[1];
+    out->t_sectors = (int64_t)c[2];
+    out->table_sectors = (int64_t)c[3];
+    out->rays = (int64_t)K->width * K->height;
+    out->rays_hit = (int64_t)hits;
+    return TSDF_OK;
+}
+
 tsdf_status tsdf_quadratic_variance(const float* depth, int64_t n, float sigma_coeff, float* var_out,
                                     void* stream) {
     if (n < 0 || (n > 0 && (!depth || !var_out)) || !(std::isfinite(sigma_coeff) && sigma_coeff >= 0.0f))

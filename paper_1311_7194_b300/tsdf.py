@@ -22,7 +22,7 @@ STORAGE_F32, STORAGE_F16, STORAGE_SNORM16 = 0, 1, 2
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
-            "tsdf_raycast_noalloc", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
+            "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
             "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
             "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
             "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
@@ -72,6 +72,14 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class RaycastCounts(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_int64), ("table_lookups", ctypes.c_int64), ("t_sectors", ctypes.c_int64),
+                ("table_sectors", ctypes.c_int64), ("rays", ctypes.c_int64), ("rays_hit", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 _lib: Optional[ctypes.CDLL] = None
 _P = ctypes.c_void_p
 _PD = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +108,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                                 ctypes.POINTER(Intrinsics), _PD, _P]),
         "tsdf_raycast": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
         "tsdf_raycast_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
+        "tsdf_raycast_trace": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, ctypes.POINTER(RaycastCounts),
+                                              _P]),
         "tsdf_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Intrinsics), ctypes.POINTER(_P)]),
         "tsdf_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
         "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
@@ -298,6 +308,16 @@ class Volume:
                                              _dev_ptr(v, 3 * H * W, "vertex_out"), _stream(stream)),
                "tsdf_raycast_noalloc")
         return out
+
+    def raycast_trace(self, intr, pose, stream=None) -> dict:
+        """tsdf_raycast_trace: traversal counts of the raycast at ``pose``
+        (samples, table lookups, distinct 32-byte sectors of T and of the block
+        table read, rays, hits). Synchronous."""
+        K = intrinsics(intr)
+        c = RaycastCounts()
+        _check(self.lib.tsdf_raycast_trace(self.h, ctypes.byref(K), _pose(pose), ctypes.byref(c), _stream(stream)),
+               "tsdf_raycast_trace")
+        return c.as_dict()
 
     def launch_config(self) -> dict:
         c = LaunchConfig()

@@ -82,6 +82,7 @@ def test_null_arguments_are_rejected(lib):
     n = ctypes.c_int64()
     assert lib.tsdf_export(None, None, None, None, 0, ctypes.byref(n)) == tsdf.ERR_INVALID_ARG
     assert lib.tsdf_quadratic_variance(None, -1, 1e-3, None, None) == tsdf.ERR_INVALID_ARG
+    assert lib.tsdf_raycast_trace(None, ctypes.byref(K), pose, None, None) == tsdf.ERR_INVALID_ARG
     lib.tsdf_destroy(None)
 
 
