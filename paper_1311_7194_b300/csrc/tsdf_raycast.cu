@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
 // six independent normal samples are in flight at once.
 constexpr int kRcWarps = 4;          // warps per CTA
 constexpr int kQueue = 64;           // brackets per warp queue (< 32 queued + 32 pushed)
+constexpr int kRefill = 8;           // idle lanes that trigger a refill of the warp
 
 // j-th of the kFine re-scan points of the step (zt - back, zt]
 __device__ __forceinline__ float zt_minus(float zt, float back, int j) {
@@ -536,6 +537,10 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     const int tiles_x = (p.width + 7) / 8;
     const unsigned n_rays = (unsigned)(tiles_x * ((p.height + 3) / 4)) * 32u;
     const int rtiles_x = (p.width + kRangeTile - 1) / kRangeTile;
+    // t / tiles_x as __umulhi(t, tdiv), exact while t * tiles_x < 2^32 (every
+    // image up to 8192 x 8192 pixels); plain division beyond
+    const unsigned tdiv = 0xffffffffu / (unsigned)tiles_x + 1u;
+    const bool fast_div = tiles_x > 1 && (unsigned long long)(n_rays >> 5) * (unsigned)tiles_x < (1ull << 32);
     unsigned hits = 0;
     int queued = 0;     // warp-uniform
 
@@ -549,8 +554,12 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     float z = 0.f, zend = 0.f, fprev = 0.f, zl = 0.f, zstep = 0.f;
 
     for (;;) {
-        // hand out rays to idle lanes; a lane keeps drawing until it holds a ray to march
-        for (;;) {
+        // hand out rays to idle lanes once kRefill of them wait (or none is
+        // busy): a refill costs the whole warp, so it is batched; a drawing
+        // lane keeps drawing until it holds a ray to march
+        const unsigned waiting = __ballot_sync(0xffffffffu, !busy && rays_left);
+        const bool refill = __popc(waiting) >= kRefill || (waiting && !__any_sync(0xffffffffu, busy));
+        for (; refill;) {
             const bool need = !busy && rays_left;
             const unsigned msk = __ballot_sync(0xffffffffu, need);
             if (!msk) break;
@@ -563,11 +572,13 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
                 rays_left = false;
                 continue;
             }
-            const int t = (int)(idx >> 5), w = (int)(idx & 31u);
-            const int u = (t % tiles_x) * 8 + (w & 7), v = (t / tiles_x) * 4 + (w >> 3);
+            const unsigned t = idx >> 5, w = idx & 31u;
+            const unsigned ty = fast_div ? __umulhi(t, tdiv) : t / (unsigned)tiles_x;
+            const unsigned tx = t - ty * (unsigned)tiles_x;
+            const int u = (int)(tx * 8u + (w & 7u)), v = (int)(ty * 4u + (w >> 3));
             if (u >= p.width || v >= p.height) continue;
             pix = v * p.width + u;
-            const int tile = (v / kRangeTile) * rtiles_x + u / kRangeTile;
+            const int tile = (v >> 2) * rtiles_x + (u >> 2);   // 4x4-pixel range tiles
             const float zn = __uint_as_float(near_[tile]), zf = __uint_as_float(far_[tile]);
             z = fmaxf(zn, p.near_clip);
             zend = fminf(zf, p.far_clip);
