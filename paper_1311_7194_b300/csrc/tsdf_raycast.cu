@@ -158,9 +158,13 @@ __device__ __forceinline__ int slot_of(const FrameParams& p, const int* __restri
     return __ldg(table + (unsigned)bx + (unsigned)p.nb * ((unsigned)by + (unsigned)p.nb * (unsigned)bz));
 }
 
-template <int kS>
+// kNarrow: the pool index slot * 512 + off fits 32 bits (capacity <= 2^23
+// blocks), which saves the 64-bit multiply per corner
+template <int kS, bool kNarrow>
 __device__ __forceinline__ float voxel(const typename Codec<kS>::E* __restrict__ T, int slot, int off, float2 sc) {
-    return slot < 0 ? __int_as_float(0x7fc00000) : Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, sc);
+    if (slot < 0) return __int_as_float(0x7fc00000);
+    if (kNarrow) return Codec<kS>::load(T + ((unsigned)slot * (unsigned)kBlockVoxels + (unsigned)off), sc);
+    return Codec<kS>::load(T + (size_t)slot * kBlockVoxels + off, sc);
 }
 
 // Traversal tracing (tsdf_raycast_trace only; compiled out of every other
@@ -194,7 +198,7 @@ __device__ __forceinline__ void trace_lookup(const FrameParams& p, int bx, int b
 // The 8 corners are fetched by the same instructions whether or not the cell
 // crosses a block face (only the extra block lookups are conditional), which
 // keeps the lanes of a warp together.
-template <int kS, bool kTrace = false>
+template <int kS, bool kTrace = false, bool kNarrow = false>
 __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __restrict__ table,
                                          const typename Codec<kS>::E* __restrict__ T, float qx, float qy, float qz,
                                          float* f, int* blk) {
@@ -245,10 +249,10 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
         trace_corner<kS>(s001, x0 + y0 + z1); trace_corner<kS>(s101, x1 + y0 + z1);
         trace_corner<kS>(s011, x0 + y1 + z1); trace_corner<kS>(s111, x1 + y1 + z1);
     }
-    const float c000 = voxel<kS>(T, s000, x0 + y0 + z0, sc), c100 = voxel<kS>(T, s100, x1 + y0 + z0, sc);
-    const float c010 = voxel<kS>(T, s010, x0 + y1 + z0, sc), c110 = voxel<kS>(T, s110, x1 + y1 + z0, sc);
-    const float c001 = voxel<kS>(T, s001, x0 + y0 + z1, sc), c101 = voxel<kS>(T, s101, x1 + y0 + z1, sc);
-    const float c011 = voxel<kS>(T, s011, x0 + y1 + z1, sc), c111 = voxel<kS>(T, s111, x1 + y1 + z1, sc);
+    const float c000 = voxel<kS, kNarrow>(T, s000, x0 + y0 + z0, sc), c100 = voxel<kS, kNarrow>(T, s100, x1 + y0 + z0, sc);
+    const float c010 = voxel<kS, kNarrow>(T, s010, x0 + y1 + z0, sc), c110 = voxel<kS, kNarrow>(T, s110, x1 + y1 + z0, sc);
+    const float c001 = voxel<kS, kNarrow>(T, s001, x0 + y0 + z1, sc), c101 = voxel<kS, kNarrow>(T, s101, x1 + y0 + z1, sc);
+    const float c011 = voxel<kS, kNarrow>(T, s011, x0 + y1 + z1, sc), c111 = voxel<kS, kNarrow>(T, s111, x1 + y1 + z1, sc);
     const float tx = qx - fx0, ty = qy - fy0, tz = qz - fz0;
     const float c00 = __fmaf_rn(tx, c100 - c000, c000);
     const float c10 = __fmaf_rn(tx, c110 - c010, c010);
@@ -466,7 +470,7 @@ __device__ __forceinline__ float zt_minus(float zt, float back, int j) {
     return zt - back + (float)j * (back / (float)kFine);
 }
 
-template <int kS>
+template <int kS, bool kNarrow>
 __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int* __restrict__ table,
                                                  const typename Codec<kS>::E* __restrict__ T, int pix, float z1,
                                                  float f1, float z2, float f2, float dqx, float dqy, float dqz,
@@ -479,7 +483,7 @@ __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int
     float zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
     for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
         float fs;
-        if (trilinear<kS>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
+        if (trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
                           __fmaf_rn(zs, dqz, p.q0[2]), &fs, blk) != 0)
             break;
         if (fs > 0.0f) {
@@ -496,12 +500,12 @@ __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int
     }
     const float qx = __fmaf_rn(zs, dqx, p.q0[0]), qy = __fmaf_rn(zs, dqy, p.q0[1]), qz = __fmaf_rn(zs, dqz, p.q0[2]);
     float fp[3], fm[3];
-    const int s0 = trilinear<kS>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk);
-    const int s1 = trilinear<kS>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk);
-    const int s2 = trilinear<kS>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk);
-    const int s3 = trilinear<kS>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk);
-    const int s4 = trilinear<kS>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk);
-    const int s5 = trilinear<kS>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk);
+    const int s0 = trilinear<kS, false, kNarrow>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk);
+    const int s1 = trilinear<kS, false, kNarrow>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk);
+    const int s2 = trilinear<kS, false, kNarrow>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk);
+    const int s3 = trilinear<kS, false, kNarrow>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk);
+    const int s4 = trilinear<kS, false, kNarrow>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk);
+    const int s5 = trilinear<kS, false, kNarrow>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk);
     float n0 = nanf_, n1 = nanf_, n2 = nanf_;
     if ((s0 | s1 | s2 | s3 | s4 | s5) == 0) {
         const float g0 = fp[0] - fm[0], g1 = fp[1] - fm[1], g2 = fp[2] - fm[2];
@@ -521,7 +525,7 @@ __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int
     }
 }
 
-template <int kS>
+template <int kS, bool kNarrow>
 __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
     const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
@@ -544,13 +548,14 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     unsigned hits = 0;
     int queued = 0;     // warp-uniform
 
-    // The march state of a lane's ray, kept small (the kernel is latency-bound
-    // and registers decide how many warps an SM holds): zl is the camera z of
-    // the last sample taken (the bracket's near end when that sample was
-    // defined), zstep the step since; the re-scan runs inline.
+    // The march state of a lane's ray, kept small (registers decide how many
+    // warps an SM holds): zl is the camera z of the last sample taken (the
+    // bracket's near end when that sample was defined), zstep the step since,
+    // iv the inverse ray direction used by empty-space skips; the re-scan runs
+    // inline.
     bool busy = false, prev_def = false, rays_left = true;
     int pix = 0, it = 0;
-    float dqx = 0.f, dqy = 0.f, dqz = 0.f;
+    float dqx = 0.f, dqy = 0.f, dqz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f;
     float z = 0.f, zend = 0.f, fprev = 0.f, zl = 0.f, zstep = 0.f;
 
     for (;;) {
@@ -592,6 +597,9 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             dqx = p.Rs[0] * dcx + p.Rs[1] * dcy + p.Rs[2];
             dqy = p.Rs[3] * dcx + p.Rs[4] * dcy + p.Rs[5];
             dqz = p.Rs[6] * dcx + p.Rs[7] * dcy + p.Rs[8];
+            ivx = dqx != 0.0f ? 1.0f / dqx : 0.0f;
+            ivy = dqy != 0.0f ? 1.0f / dqy : 0.0f;
+            ivz = dqz != 0.0f ? 1.0f / dqz : 0.0f;
             prev_def = false;
             fprev = 0.0f;
             zl = z;
@@ -607,7 +615,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             queued -= n;
             if (lane < n) {
                 const int e = queued + lane;
-                refine_and_shade<kS>(p, table, T, __float_as_int(q[0][e]), q[1][e], q[2][e], q[3][e], q[4][e],
+                refine_and_shade<kS, kNarrow>(p, table, T, __float_as_int(q[0][e]), q[1][e], q[2][e], q[3][e], q[4][e],
                                      q[5][e], q[6][e], q[7][e], depth_out, normal_out, vertex_out);
                 ++hits;
             }
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
         // one march sample per busy lane
         float f = 0.0f;
         int blk[3] = {0, 0, 0};
-        const int st = busy ? trilinear<kS>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
+        const int st = busy ? trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
                                             __fmaf_rn(z, dqz, p.q0[2]), &f, blk)
                             : 0;
         bool miss = false, push = false;
@@ -626,8 +634,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
         if (busy) {
             bool done = false;
             if (st == 2) {
-                const float inv[3] = {dqx != 0.0f ? 1.0f / dqx : 0.0f, dqy != 0.0f ? 1.0f / dqy : 0.0f,
-                                      dqz != 0.0f ? 1.0f / dqz : 0.0f};
+                const float inv[3] = {ivx, ivy, ivz};
                 zl = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
                 z = zl + 1e-3f * h;
                 zstep = z - zl;
@@ -644,7 +651,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
                         const float zq = j == kFine ? z : zt_minus(z, back, j);
                         float fq = f;
                         const int sq_ = j == kFine ? 0
-                                                   : trilinear<kS>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
+                                                   : trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
                                                                    __fmaf_rn(zq, dqy, p.q0[1]),
                                                                    __fmaf_rn(zq, dqz, p.q0[2]), &fq, blk);
                         if (sq_ != 0) {
@@ -723,20 +730,30 @@ void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
 }
 
 // Raycast tile shapes the autotuner chooses from (pixels per CTA, width x height).
+template <int kS, bool kNarrow>
+void launch_persistent(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
+                       float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    // exactly the CTAs that fit at once: a CTA launched later would find no rays left
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_persistent_kernel<kS, kNarrow>, 32 * kRcWarps,
+                                                       0) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    raycast_persistent_kernel<kS, kNarrow><<<v->num_sms * per_sm, 32 * kRcWarps, 0, st>>>(
+        p, near_, far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
+        normal_out, vertex_out, v->ctr);
+}
+
 template <int kS>
 void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     if (v->lc.raycast_persistent) {
-        // exactly the CTAs that fit at once: a CTA launched later would find no rays left
-        static int per_sm = 0;
-        if (per_sm == 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raycast_persistent_kernel<kS>, 32 * kRcWarps, 0) !=
-                 cudaSuccess ||
-             per_sm < 1))
-            per_sm = 1;
-        raycast_persistent_kernel<kS><<<v->num_sms * per_sm, 32 * kRcWarps, 0, st>>>(
-            p, near_, far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
-            normal_out, vertex_out, v->ctr);
+        if (v->cfg.block_capacity <= ((int64_t)1 << 23)) {
+            launch_persistent<kS, true>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+        } else {
+            launch_persistent<kS, false>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+        }
         return;
     }
     const int tw = v->lc.raycast_tile_w, th = v->lc.raycast_tile_h;

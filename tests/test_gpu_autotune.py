@@ -75,3 +75,21 @@ def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
     vol2 = tsdf.Volume.from_params(seq.volume)
     shape2, hit2 = vol2.autotune(d, seq.intr, seq.poses, cache)
     assert hit2 and shape2 == shape and vol2.launch_config() == shape
+
+
+def test_persistent_raycast_with_a_pool_beyond_32_bit_voxel_indices():
+    """Pools of more than 2^23 blocks (2^32 voxels) take the persistent kernel
+    with 64-bit voxel indexing; it must agree with the per-pixel kernel."""
+    seq = synth.room_sequence(n_frames=4, width=157, height=117, grid_dim=512, voxel_size=6e-3,
+                              block_capacity=(1 << 23) + 8)
+    vol = tsdf.Volume.from_params(seq.volume, storage=tsdf.STORAGE_F16)    # 3 KB per block: 25 GB
+    for k in range(seq.n_frames):
+        vol.fuse(torch.from_numpy(seq.depth[k]).cuda(), seq.intr, seq.poses[k])
+    maps = {}
+    for persistent in (0, 1):
+        vol.set_launch_config(raycast_persistent=persistent)
+        maps[persistent] = [t.cpu().numpy() for t in vol.raycast(seq.intr, seq.poses[-1])]
+    for a, b in zip(maps[0], maps[1]):
+        assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+    assert (maps[1][0] > 0).sum() > 5000
+    vol.close()
