@@ -60,7 +60,8 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
         const float z = oc[2] + ax * p.cs[6] + ay * p.cs[7] + az * p.cs[8];
         zmin = fminf(zmin, z);
         zmax = fmaxf(zmax, z);
-        const float rz = 1.0f / fmaxf(z, 1e-20f);
+        float rz;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(fmaxf(z, 1e-20f)));   // the rect is padded by a pixel
         const float u = p.fx * x * rz + p.cx, v = p.fy * y * rz + p.cy;
         umin = fminf(umin, u); umax = fmaxf(umax, u);
         vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
@@ -143,16 +144,28 @@ __device__ __forceinline__ bool band_reachable(const FrameParams& p, const float
 // block can have T_k != chi in that frame.
 __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* __restrict__ tiles, int4 bc, int slot,
                                            VisibleBlock* e) {
-    double o[3];
-    cam_block_origin(p, bc, o);
-    const float of[3] = {(float)o[0], (float)o[1], (float)o[2]};
+    // visibility from a float32 camera position of the block's first voxel
+    // (a few ulps from the double one: far inside the pixel of padding and the
+    // band slack); the double position only for blocks that pass
+    float of[3];
+    const float bx = (float)(kSide * bc.x), by = (float)(kSide * bc.y), bz = (float)(kSide * bc.z);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        of[r] = __fmaf_rn(bz, p.cs[3 * r + 2], __fmaf_rn(by, p.cs[3 * r + 1], __fmaf_rn(bx, p.cs[3 * r], p.oc0[r])));
     float zmin, zmax, rect[4];
     float zlo = -3.0e38f, zhi = 3.0e38f;
     bool keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
     if (keep && rect[0] > -1e29f) keep = band_reachable(p, tiles, rect, zmin, zmax, &zlo, &zhi);
     e->slot = slot;
+    double oz = (double)of[2];
+    if (keep) {
+        double o[3];
+        cam_block_origin(p, bc, o);
+        for (int r = 0; r < 3; ++r) of[r] = (float)o[r];
+        oz = o[2];
+    }
     for (int r = 0; r < 3; ++r) e->o[r] = of[r];
-    e->oz_lo = (float)(o[2] - (double)of[2]);
+    e->oz_lo = (float)(oz - (double)of[2]);
     e->zlo = keep ? zlo : 3.0e38f;     // an empty range makes every voxel chi
     e->zhi = keep ? zhi : -3.0e38f;
     e->pad = 0;
