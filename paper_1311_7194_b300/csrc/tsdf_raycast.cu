@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             const int u = (int)(tx * 8u + (w & 7u)), v = (int)(ty * 4u + (w >> 3));
             if (u >= p.width || v >= p.height) continue;
             pix = v * p.width + u;
-            const int tile = (v >> 2) * rtiles_x + (u >> 2);   // 4x4-pixel range tiles
+            const int tile = (int)((unsigned)v / kRangeTile) * rtiles_x + (int)((unsigned)u / kRangeTile);
             const float zn = __uint_as_float(near_[tile]), zf = __uint_as_float(far_[tile]);
             z = fmaxf(zn, p.near_clip);
             zend = fminf(zf, p.far_clip);
