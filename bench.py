@@ -57,9 +57,10 @@ def parse():
                     help="storage of T for --workload capsules")
     ap.add_argument("--oracle-sample", type=int, default=0,
                     help="capsules: compare this many sampled voxels with the FP64 oracle (per-voxel replay)")
-    ap.add_argument("--workload", choices=["room", "batched", "capsules"], default="room",
+    ap.add_argument("--workload", choices=["room", "batched", "capsules", "sphere"], default="room",
                     help="room: per-frame live fusion (2048^3, 1.5 mm); batched: 3000^3 grid of 1 mm voxels, "
-                         "1000 frames fused K=8 per graph launch, raycast per batch")
+                         "1000 frames fused K=8 per graph launch, raycast per batch; capsules: 1280x1024 "
+                         "small objects on a 4096^3 grid of 0.15 mm voxels; sphere: the 160x120 parity scene")
     ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
     ap.add_argument("--cpu-ray-stride", type=int, default=8, help="oracle sample: pixel stride per axis")
     return ap.parse_args()
@@ -501,10 +502,11 @@ def run_batched(args):
 
 
 def run_capsules(args):
-    """High-resolution small object: 1280x1024, 4096^3 grid of 0.15 mm voxels,
-    200 frames, T stored as float32, FP16 or snorm16 (P float32), one graph
-    launch per frame; optionally the error of sampled voxels against the FP64
-    oracle."""
+    """Small scenes, one graph launch per frame, T stored as float32, FP16 or
+    snorm16 (P float32); optionally the error of sampled voxels against the
+    FP64 oracle. capsules: high-resolution small object, 1280x1024, 4096^3 grid
+    of 0.15 mm voxels, 200 frames; sphere: the tiny parity scene, 160x120,
+    256^3 grid of 1 mm voxels, 10 frames."""
     import numpy as np
     import torch
 
@@ -516,8 +518,14 @@ def run_capsules(args):
     dev = torch.device("cuda", 0)
     pkg_build.build()
     storage = {"f32": tsdf.STORAGE_F32, "f16": tsdf.STORAGE_F16, "snorm16": tsdf.STORAGE_SNORM16}[args.storage]
-    n = args.frames if args.frames != 300 else 200
-    seq = synth.capsule_sequence(n_frames=n, device=dev, block_capacity=args.block_capacity or (1 << 20))
+    if args.workload == "sphere":
+        n = args.frames if args.frames != 300 else 10
+        seq = synth.sphere_sequence(n_frames=n, device=dev)
+        name = f"tiny sphere: 160x120, 256^3 grid of 1 mm voxels, {n} frames"
+    else:
+        n = args.frames if args.frames != 300 else 200
+        seq = synth.capsule_sequence(n_frames=n, device=dev, block_capacity=args.block_capacity or (1 << 20))
+        name = f"high-res small object: 1280x1024, 4096^3 grid of 0.15 mm voxels, {n} frames"
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume, storage=storage)
@@ -547,8 +555,7 @@ def run_capsules(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f16 T / f32 P", 2: "snorm16 T / f32 P"}[storage],
             "data": "synthetic",
-            "config": {"workload": f"high-res small object: 1280x1024, 4096^3 grid of 0.15 mm voxels, {F} frames",
-                       "storage": args.storage, "frames_per_step": F},
+            "config": {"workload": name, "storage": args.storage, "frames_per_step": F},
             "voxel_updates_per_s": st["voxel_updates_total"] * args.steps / sec,
             "rays_per_s": F * H * W * args.steps / sec,
             "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "blocks": int(st["n_blocks"])},
@@ -592,7 +599,7 @@ def main():
         raise SystemExit(f"--workload {args.workload} is a single-GPU measurement; run it without torchrun")
     elif args.workload == "batched":
         run_batched(args)
-    elif args.workload == "capsules":
+    elif args.workload in ("capsules", "sphere"):
         run_capsules(args)
     else:
         run_ours(args)
