@@ -60,6 +60,21 @@ typedef enum {
                                    T = q * (delta/32767), chi = -32768: 6 bytes per voxel */
 } tsdf_storage;
 
+/* How a measurement T_k(x) enters the voxel (section "Integration of
+ * Measurements"). Every rule starts a chi voxel at T_k and marks |T| > delta as
+ * chi afterwards.
+ *   KALMAN:   Alg. 3 (the default): P <- P + Q, K = P / (P + p_k),
+ *             T <- T + K (T_k - T), P <- (1 - K) P; P is the pool's second array.
+ *   AVERAGE:  Alg. 1: T <- (1 - w) T + w T_k with the fixed weight
+ *             w = update_weight; the second array is neither read nor written.
+ *   WEIGHTED: Alg. 2: T <- (W T + w T_k) / (W + w), W <- min(W + w, W_max), with
+ *             W kept in the second array (first measurement: W = w). */
+typedef enum {
+    TSDF_UPDATE_KALMAN = 0,
+    TSDF_UPDATE_AVERAGE = 1,
+    TSDF_UPDATE_WEIGHTED = 2
+} tsdf_update_rule;
+
 /* Pinhole intrinsics of one depth map / output map. */
 typedef struct {
     float fx, fy, cx, cy;
@@ -82,6 +97,10 @@ typedef struct {
                                    variance map is given (default 1.5e-3) */
     int32_t storage;            /* tsdf_storage (default TSDF_STORAGE_F32) */
     int32_t alloc_half_samples; /* J >= 0; 0 = ceil(2 delta / s) (default 0) */
+    int32_t update_rule;        /* tsdf_update_rule (default TSDF_UPDATE_KALMAN) */
+    float update_weight;        /* w_k of Alg. 1 (0 < w <= 1) and Alg. 2 (w > 0),
+                                   the same for every measurement (default 0.1) */
+    float weight_max;           /* W_max >= w of Alg. 2 (default 1) */
 } tsdf_config;
 
 /* Counters of the last calls (tsdf_get_stats). */

@@ -55,7 +55,8 @@ class _Params(ctypes.Structure):
                 ("raycast_near", ctypes.c_float), ("raycast_far", ctypes.c_float),
                 ("sigma_coeff", ctypes.c_float), ("alloc_half_samples", ctypes.c_int32),
                 ("amb_px", ctypes.c_double), ("amb_trunc", ctypes.c_double),
-                ("store_values", ctypes.c_int32)]
+                ("store_values", ctypes.c_int32), ("update_rule", ctypes.c_int32),
+                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float)]
 
 
 class _Intr(ctypes.Structure):
@@ -135,6 +136,9 @@ def make_params(vol, amb_px: float = 1e-3, amb_trunc: float = 1e-5, store_values
     p.alloc_half_samples = int(alloc_half_samples)
     p.amb_px, p.amb_trunc = float(amb_px), float(amb_trunc)
     p.store_values = int(bool(store_values))
+    p.update_rule = int(getattr(vol, "update_rule", 0))
+    p.update_weight = float(getattr(vol, "update_weight", 0.1))
+    p.weight_max = float(getattr(vol, "weight_max", 1.0))
     return p
 
 

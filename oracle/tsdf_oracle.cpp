@@ -23,6 +23,10 @@
 //     projecting x into the measured depth map; chi when there is no measurement.
 //   * Alg. 3 (Kalman filter for TSDF estimation): predict P+Q, gain K, correct T,
 //     shrink P, then chi if |T| > delta.
+//   * Alg. 1 (scene TSDF estimation): T <- (1 - w_k) T + w_k T_k, chi if |T| > delta.
+//   * Alg. 2 (weighted scene TSDF estimation): T <- (W T + w_k T_k) / (W + w_k),
+//     W <- min(W + w_k, W_max), chi if |T| > delta; the weight W is kept where
+//     Alg. 3 keeps P.
 //   * Eq. 9: averaging N measurements of deviation sigma leaves variance sigma^2/N
 //     (used by the tests as a closed-form pin).
 //   * Section "Scene Rendering": the depth/normal map of the fused surface is found
@@ -64,6 +68,10 @@ struct ov_params {
     double amb_px;              // pixel-rounding ambiguity margin, pixels
     double amb_trunc;           // truncation-test ambiguity margin, fraction of delta
     int32_t store_values;       // 0 = allocation bookkeeping only
+    int32_t update_rule;        // 0 = Alg. 3 (Kalman), 1 = Alg. 1 (running average),
+                                // 2 = Alg. 2 (weighted average with W_max)
+    float update_weight;        // w_k of Alg. 1 / Alg. 2 (the same for every measurement)
+    float weight_max;           // W_max of Alg. 2
 };
 
 struct ov_intr {
@@ -347,6 +355,41 @@ void kalman_update(double& T, double& P, uint8_t& chi, double Tk, double pk, dou
     if (std::fabs(T) > delta) chi = 1;
 }
 
+// Alg. 1: a fixed-weight running average of the measurements. P is not used.
+void average_update(double& T, uint8_t& chi, double Tk, double w, double delta) {
+    if (chi) {
+        T = Tk;
+        chi = 0;
+    } else {
+        T = (1.0 - w) * T + w * Tk;
+    }
+    if (std::fabs(T) > delta) chi = 1;
+}
+
+// Alg. 2: the weighted average, with the weight sum W (held in P) bounded by W_max.
+void weighted_update(double& T, double& W, uint8_t& chi, double Tk, double w, double Wmax, double delta) {
+    if (chi) {
+        T = Tk;
+        W = w;
+        chi = 0;
+    } else {
+        T = (W * T + w * Tk) / (W + w);
+        W = std::min(W + w, Wmax);
+    }
+    if (std::fabs(T) > delta) chi = 1;
+}
+
+// One measurement into one voxel by the volume's update rule.
+void update_voxel(const ov_params& p, double& T, double& P, uint8_t& chi, double Tk, double pk) {
+    const double delta = (double)p.truncation;
+    if (p.update_rule == 1)
+        average_update(T, chi, Tk, (double)p.update_weight, delta);
+    else if (p.update_rule == 2)
+        weighted_update(T, P, chi, Tk, (double)p.update_weight, (double)p.weight_max, delta);
+    else
+        kalman_update(T, P, chi, Tk, pk, (double)p.process_variance, delta);
+}
+
 // --------------------------------------------------------------------------
 // Raycast (section "Scene Rendering")
 // --------------------------------------------------------------------------
@@ -575,13 +618,13 @@ void ov_allocate(void* h, const float* depth, const ov_intr* in, const double* p
     add_blocks(v, frame_blocks(v.p, depth, *in, pose), frame, n_new, overflow);
 }
 
-// Alg. 3 over every voxel of every allocated block (no culling).
+// The update rule (Alg. 3 by default) over every voxel of every allocated block
+// (no culling).
 void ov_integrate(void* h, const float* depth, const float* var, const ov_intr* in,
                   const double* pose) {
     Volume& v = *static_cast<Volume*>(h);
     if (!v.p.store_values) return;
     const Frame f = make_frame(depth, var, *in, pose);
-    const double Q = (double)v.p.process_variance, delta = (double)v.p.truncation;
     const int64_t nblk = (int64_t)v.blocks.size();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t bi = 0; bi < nblk; ++bi) {
@@ -593,7 +636,7 @@ void ov_integrate(void* h, const float* depth, const float* var, const ov_intr* 
             const Meas m = measure(v.p, f, ix, iy, iz);
             if (m.amb) b.amb[l] = 1;
             if (!m.valid) continue;
-            kalman_update(b.T[l], b.P[l], b.chi[l], m.Tk, m.pk, Q, delta);
+            update_voxel(v.p, b.T[l], b.P[l], b.chi[l], m.Tk, m.pk);
         }
     }
 }
@@ -650,13 +693,13 @@ void ov_field(const void* h, int64_t n, const double* points, double* f) {
 
 // Per-voxel replay of a whole sequence: for each listed voxel (ix, iy, iz) whose
 // block joined the pool at frame alloc_frame[k], apply every frame from that one
-// on with Alg. 3. Gives the same values ov_integrate would, one voxel at a time.
+// on with the volume's update rule. Gives the same values ov_integrate would, one
+// voxel at a time.
 void ov_replay_voxels(const ov_params* p, int32_t n_frames, const float* const* depths,
                       const float* const* vars, const ov_intr* in, const double* poses,
                       int64_t n, const int32_t* voxels, const int32_t* alloc_frame,
                       double* T_out, double* P_out, uint8_t* amb_out) {
     const double nan = std::numeric_limits<double>::quiet_NaN();
-    const double Q = (double)p->process_variance, delta = (double)p->truncation;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t k = 0; k < n; ++k) {
         double T = 0.0, P = 0.0;
@@ -665,7 +708,7 @@ void ov_replay_voxels(const ov_params* p, int32_t n_frames, const float* const* 
             const Frame f = make_frame(depths[fi], vars ? vars[fi] : nullptr, *in, poses + 16 * fi);
             const Meas m = measure(*p, f, voxels[3 * k], voxels[3 * k + 1], voxels[3 * k + 2]);
             if (m.amb) amb = 1;
-            if (m.valid) kalman_update(T, P, chi, m.Tk, m.pk, Q, delta);
+            if (m.valid) update_voxel(*p, T, P, chi, m.Tk, m.pk);
         }
         T_out[k] = chi ? nan : T;
         P_out[k] = chi ? nan : P;
@@ -673,7 +716,8 @@ void ov_replay_voxels(const ov_params* p, int32_t n_frames, const float* const* 
     }
 }
 
-// Dense brute force: Alg. 3 applied to every voxel of a G^3 grid, no allocation.
+// Dense brute force: the update rule applied to every voxel of a G^3 grid, no
+// allocation.
 void* ov_dense_create(const ov_params* p) {
     if (!p || p->grid_dim <= 0) return nullptr;
     Volume* v = new Volume();
@@ -693,7 +737,6 @@ void ov_dense_integrate(void* h, const float* depth, const float* var, const ov_
     Volume& v = *static_cast<Volume*>(h);
     const Frame f = make_frame(depth, var, *in, pose);
     const int64_t G = v.p.grid_dim;
-    const double Q = (double)v.p.process_variance, delta = (double)v.p.truncation;
     Block& b = v.blocks[0];
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t iz = 0; iz < G; ++iz)
@@ -702,7 +745,7 @@ void ov_dense_integrate(void* h, const float* depth, const float* var, const ov_
                 const size_t l = (size_t)(ix + G * (iy + G * iz));
                 const Meas m = measure(v.p, f, ix, iy, iz);
                 if (m.amb) b.amb[l] = 1;
-                if (m.valid) kalman_update(b.T[l], b.P[l], b.chi[l], m.Tk, m.pk, Q, delta);
+                if (m.valid) update_voxel(v.p, b.T[l], b.P[l], b.chi[l], m.Tk, m.pk);
             }
 }
 

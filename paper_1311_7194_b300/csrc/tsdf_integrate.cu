@@ -280,23 +280,35 @@ __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock
     return true;
 }
 
-// Alg. 3 for one voxel: chi is NaN. (1 - K) P is formed as P p_k / (P + p_k),
-// the same quantity without the cancellation of 1 - K when K is near 1.
-__device__ __forceinline__ void kalman(float& T, float& P, float Tk, float pk, float Q, float delta) {
+// One measurement into one voxel, chi is NaN; kRule is a tsdf_update_rule.
+//   Alg. 3 (Kalman): (1 - K) P is formed as P p_k / (P + p_k), the same quantity
+//     without the cancellation of 1 - K when K is near 1.
+//   Alg. 1 (running average): T <- (1 - w) T + w T_k; P untouched.
+//   Alg. 2 (weighted average): T <- (W T + w T_k) / (W + w), W <- min(W + w, W_max),
+//     with W in P.
+template <int kRule>
+__device__ __forceinline__ void update(const FrameParams& p, float& T, float& P, float Tk, float pk) {
     if (isnan(T)) {
         T = Tk;
-        P = pk;
-    } else {
-        P = __fadd_rn(P, Q);                              // predict
+        if (kRule == TSDF_UPDATE_KALMAN) P = pk;
+        if (kRule == TSDF_UPDATE_WEIGHTED) P = p.w;
+    } else if (kRule == TSDF_UPDATE_KALMAN) {
+        P = __fadd_rn(P, p.Q);                            // predict
         const float r = rcp_approx(__fadd_rn(P, pk));
         const float K = __fmul_rn(P, r);                  // gain P / (P + p_k)
         T = __fmaf_rn(K, __fsub_rn(Tk, T), T);            // correct
         P = __fmul_rn(P, __fmul_rn(pk, r));               // (1 - K) P, as P p_k / (P + p_k)
+    } else if (kRule == TSDF_UPDATE_AVERAGE) {
+        T = __fmaf_rn(p.w, __fsub_rn(Tk, T), T);          // (1 - w) T + w T_k
+    } else {
+        const float Wn = __fadd_rn(P, p.w);
+        T = __fdiv_rn(__fmaf_rn(P, T, __fmul_rn(p.w, Tk)), Wn);
+        P = fminf(Wn, p.wmax);
     }
-    if (fabsf(T) > delta) T = __int_as_float(0x7fc00000);
+    if (fabsf(T) > p.delta) T = __int_as_float(0x7fc00000);
 }
 
-template <bool kVarMap, int kS, int kVPT>
+template <bool kVarMap, int kS, int kVPT, int kRule>
 __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters* __restrict__ ctr,
                                                                         const VisibleBlock* __restrict__ vis,
                                                                         typename Codec<kS>::E* __restrict__ T,
@@ -328,20 +340,22 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters
 #pragma unroll
         for (int g = 0; g < kVPT; g += 4) {
             Codec<kS>::load4(T + off + g, tv + g, p.tsc);
-            const float4 p4 = *reinterpret_cast<const float4*>(P + off + g);
+            float4 p4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (kRule != TSDF_UPDATE_AVERAGE) p4 = *reinterpret_cast<const float4*>(P + off + g);
             pv[g] = p4.x; pv[g + 1] = p4.y; pv[g + 2] = p4.z; pv[g + 3] = p4.w;
         }
 #pragma unroll
         for (int e = 0; e < kVPT; ++e) {
             if (ok[e]) {
-                kalman(tv[e], pv[e], tk[e], pk[e], p.Q, p.delta);
+                update<kRule>(p, tv[e], pv[e], tk[e], pk[e]);
                 ++updates;
             }
         }
 #pragma unroll
         for (int g = 0; g < kVPT; g += 4) {
             Codec<kS>::store4(T + off + g, tv + g, p.tsc);
-            *reinterpret_cast<float4*>(P + off + g) = make_float4(pv[g], pv[g + 1], pv[g + 2], pv[g + 3]);
+            if (kRule != TSDF_UPDATE_AVERAGE)
+                *reinterpret_cast<float4*>(P + off + g) = make_float4(pv[g], pv[g + 1], pv[g + 2], pv[g + 3]);
         }
     }
     updates = warp_sum(updates);
@@ -353,7 +367,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters
 // before the block's allocation - and stored once. Same measurement and update
 // functions as integrate_kernel, so the result equals K sequential calls bit
 // for bit.
-template <bool kVarMap, int kS>
+template <bool kVarMap, int kS, int kRule>
 __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
                                                                             const VisibleBlock* __restrict__ vis,
                                                                             const int4* __restrict__ blocks,
@@ -387,21 +401,23 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             if (!any) continue;
             if (!loaded) {
                 Codec<kS>::load4(T + off, tv, bp.fp[0].tsc);
-                const float4 p4 = *reinterpret_cast<const float4*>(P + off);
+                float4 p4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (kRule != TSDF_UPDATE_AVERAGE) p4 = *reinterpret_cast<const float4*>(P + off);
                 pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
                 loaded = true;
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (ok[e]) {
-                    kalman(tv[e], pv[e], tk[e], pk[e], p.Q, p.delta);
+                    update<kRule>(p, tv[e], pv[e], tk[e], pk[e]);
                     ++updates;
                 }
             }
         }
         if (loaded) {
             Codec<kS>::store4(T + off, tv, bp.fp[0].tsc);
-            *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            if (kRule != TSDF_UPDATE_AVERAGE)
+                *reinterpret_cast<float4*>(P + off) = make_float4(pv[0], pv[1], pv[2], pv[3]);
         }
     }
     updates = warp_sum(updates);
@@ -415,15 +431,25 @@ __global__ void reset_frame_counters(Counters* ctr) {
     ctr->voxel_updates = 0;
 }
 
-template <int kS, int kVPT>
-void launch_integrate_v(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+template <int kS, int kVPT, int kRule>
+void launch_integrate_r(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
                         cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     constexpr int threads = kBlockVoxels / kVPT;
     if (var)
-        integrate_kernel<true, kS, kVPT><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+        integrate_kernel<true, kS, kVPT, kRule><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
     else
-        integrate_kernel<false, kS, kVPT><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+        integrate_kernel<false, kS, kVPT, kRule><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+}
+
+template <int kS, int kVPT>
+void launch_integrate_v(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+                        cudaStream_t st) {
+    switch (v->cfg.update_rule) {
+        case TSDF_UPDATE_AVERAGE: launch_integrate_r<kS, kVPT, TSDF_UPDATE_AVERAGE>(v, depth, var, p, grid, st); break;
+        case TSDF_UPDATE_WEIGHTED: launch_integrate_r<kS, kVPT, TSDF_UPDATE_WEIGHTED>(v, depth, var, p, grid, st); break;
+        default: launch_integrate_r<kS, kVPT, TSDF_UPDATE_KALMAN>(v, depth, var, p, grid, st); break;
+    }
 }
 
 template <int kS>
@@ -435,15 +461,24 @@ void launch_integrate_s(tsdf_volume* v, const float* depth, const float* var, co
         launch_integrate_v<kS, 4>(v, depth, var, p, grid, st);
 }
 
-template <int kS>
-void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
+template <int kS, int kRule>
+void launch_integrate_batch_r(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     if (bp.var[0])
-        integrate_batch_kernel<true, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, T,
-                                                                             v->P, bp);
+        integrate_batch_kernel<true, kS, kRule><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch,
+                                                                                    v->blocks, T, v->P, bp);
     else
-        integrate_batch_kernel<false, kS><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch, v->blocks, T,
-                                                                              v->P, bp);
+        integrate_batch_kernel<false, kS, kRule><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch,
+                                                                                     v->blocks, T, v->P, bp);
+}
+
+template <int kS>
+void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
+    switch (v->cfg.update_rule) {
+        case TSDF_UPDATE_AVERAGE: launch_integrate_batch_r<kS, TSDF_UPDATE_AVERAGE>(v, bp, grid, st); break;
+        case TSDF_UPDATE_WEIGHTED: launch_integrate_batch_r<kS, TSDF_UPDATE_WEIGHTED>(v, bp, grid, st); break;
+        default: launch_integrate_batch_r<kS, TSDF_UPDATE_KALMAN>(v, bp, grid, st); break;
+    }
 }
 
 }  // namespace

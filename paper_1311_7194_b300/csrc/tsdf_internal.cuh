@@ -81,6 +81,7 @@ struct FrameParams {
     float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;
+    float w, wmax;       // w_k and W_max of Alg. 1 / Alg. 2 (the rule itself is a kernel template argument)
     float2 tsc;          // snorm16 scales: (delta / 32767, 32767 / delta)
     float zlo, zhi;      // camera z range a block must reach to matter
     float near_clip, far_clip;

@@ -148,6 +148,8 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.delta = v->cfg.truncation;
     p.Q = v->cfg.process_variance;
     p.sigma_coeff = v->cfg.sigma_coeff;
+    p.w = v->cfg.update_weight;
+    p.wmax = v->cfg.weight_max;
     p.tsc = make_float2((float)((double)v->cfg.truncation / 32767.0), (float)(32767.0 / (double)v->cfg.truncation));
     const double dl = 1.01 * (double)v->cfg.truncation;
     p.zlo = (float)((double)v->cfg.depth_min - dl);
@@ -248,6 +250,9 @@ void tsdf_config_default(tsdf_config* c) {
     c->sigma_coeff = 1.5e-3f;
     c->storage = TSDF_STORAGE_F32;
     c->alloc_half_samples = 0;
+    c->update_rule = TSDF_UPDATE_KALMAN;
+    c->update_weight = 0.1f;
+    c->weight_max = 1.0f;
 }
 
 const char* tsdf_status_string(tsdf_status s) {
@@ -281,6 +286,14 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     if (c.storage != TSDF_STORAGE_F32 && c.storage != TSDF_STORAGE_F16 && c.storage != TSDF_STORAGE_SNORM16)
         return TSDF_ERR_INVALID_ARG;
     if (c.alloc_half_samples < 0 || c.alloc_half_samples > 4096) return TSDF_ERR_INVALID_ARG;
+    if (c.update_rule < TSDF_UPDATE_KALMAN || c.update_rule > TSDF_UPDATE_WEIGHTED) return TSDF_ERR_INVALID_ARG;
+    if (c.update_rule != TSDF_UPDATE_KALMAN) {
+        if (!(std::isfinite(c.update_weight) && c.update_weight > 0.0f)) return TSDF_ERR_INVALID_ARG;
+        if (c.update_rule == TSDF_UPDATE_AVERAGE && !(c.update_weight <= 1.0f)) return TSDF_ERR_INVALID_ARG;
+        if (c.update_rule == TSDF_UPDATE_WEIGHTED &&
+            !(std::isfinite(c.weight_max) && c.weight_max >= c.update_weight))
+            return TSDF_ERR_INVALID_ARG;
+    }
     for (int r = 0; r < 3; ++r)
         if (!std::isfinite(c.origin[r])) return TSDF_ERR_INVALID_ARG;
     if (c.alloc_half_samples == 0 && std::ceil(2.0 * c.truncation / c.voxel_size - 1e-6) > 4096.0)

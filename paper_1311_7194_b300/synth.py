@@ -65,6 +65,9 @@ class VolumeParams:
     raycast_far: float
     sigma_coeff: float          # sensor deviation sigma = sigma_coeff * z^2
     process_variance: float = 0.0
+    update_rule: int = 0        # 0 Alg. 3 (Kalman), 1 Alg. 1 (running average), 2 Alg. 2 (weighted)
+    update_weight: float = 0.1  # w_k of Alg. 1 / Alg. 2
+    weight_max: float = 1.0     # W_max of Alg. 2
 
 
 @dataclass
@@ -468,13 +471,22 @@ def capsule_sequence(seed: int = 2, n_frames: int = 200, width: int = 1280, heig
     return Sequence("capsules", seed, intr, vol, scene, poses, depth, clean)
 
 
+def noise_ramp(n_frames: int, sigma0: float, sigma1: Optional[float]) -> np.ndarray:
+    """Per-frame deviations rising linearly from sigma0 (first frame) to sigma1
+    (last frame); constant sigma0 when sigma1 is None."""
+    if sigma1 is None or n_frames < 2:
+        return np.full(n_frames, float(sigma0))
+    return sigma0 + (sigma1 - sigma0) * np.arange(n_frames) / (n_frames - 1)
+
+
 def plane_sequence(distance: float = 0.5, n_frames: int = 4, width: int = 64, height: int = 48,
                    f: float = 60.0, voxel_size: float = 2e-3, grid_dim: int = 256,
                    noise_sigma: float = 0.0, seed: int = 5, static: bool = True,
-                   offset=(0.0, 0.0, 0.0)) -> Sequence:
+                   offset=(0.0, 0.0, 0.0), noise_sigma_end: Optional[float] = None) -> Sequence:
     """Fronto-parallel plane z = ``distance`` in front of a camera at the world origin
     looking down +z. With ``static`` every frame has the identity pose; otherwise the
-    camera slides sideways. ``noise_sigma`` is a constant per-pixel deviation."""
+    camera slides sideways. Per-pixel Gaussian noise of deviation ``noise_sigma``,
+    or rising linearly to ``noise_sigma_end`` over the frames (``noise_ramp``)."""
     scene = Scene(plane_z=distance)
     poses = []
     for i in range(n_frames):
@@ -490,10 +502,11 @@ def plane_sequence(distance: float = 0.5, n_frames: int = 4, width: int = 64, he
                        raycast_near=0.01, raycast_far=10.0, sigma_coeff=0.0)
     intr = Intrinsics.centred(f, width, height)
     depth = np.empty((n_frames, height, width), np.float32)
+    sig = noise_ramp(n_frames, noise_sigma, noise_sigma_end)
     for i in range(n_frames):
         clean = render_depth(scene, intr, poses[i]).numpy()
         rng = np.random.default_rng([seed, i])
-        z = clean + (noise_sigma * rng.standard_normal(clean.shape) if noise_sigma > 0 else 0.0)
+        z = clean + (sig[i] * rng.standard_normal(clean.shape) if sig[i] > 0 else 0.0)
         depth[i] = np.where(np.isfinite(z) & (z > 0), z, 0.0).astype(np.float32)
     return Sequence("plane", seed, intr, vol, scene, poses, depth, None)
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtsdf.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_HASH_FULL, ERR_CUDA, ERR_NOT_READY, ERR_OUT_OF_MEMORY = range(7)
 STORAGE_F32, STORAGE_F16, STORAGE_SNORM16 = 0, 1, 2
+UPDATE_KALMAN, UPDATE_AVERAGE, UPDATE_WEIGHTED = 0, 1, 2      # tsdf_update_rule
 
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
@@ -43,7 +44,8 @@ class Config(ctypes.Structure):
                 ("depth_min", ctypes.c_float), ("depth_max", ctypes.c_float),
                 ("raycast_near", ctypes.c_float), ("raycast_far", ctypes.c_float),
                 ("sigma_coeff", ctypes.c_float), ("storage", ctypes.c_int32),
-                ("alloc_half_samples", ctypes.c_int32)]
+                ("alloc_half_samples", ctypes.c_int32), ("update_rule", ctypes.c_int32),
+                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float)]
 
 
 class Intrinsics(ctypes.Structure):
@@ -172,6 +174,9 @@ def config_from(vol, **overrides) -> Config:
     c.depth_min, c.depth_max = vol.depth_min, vol.depth_max
     c.raycast_near, c.raycast_far = vol.raycast_near, vol.raycast_far
     c.sigma_coeff = vol.sigma_coeff
+    c.update_rule = int(getattr(vol, "update_rule", UPDATE_KALMAN))
+    c.update_weight = float(getattr(vol, "update_weight", c.update_weight))
+    c.weight_max = float(getattr(vol, "weight_max", c.weight_max))
     for k, v in overrides.items():
         setattr(c, k, v)
     return c

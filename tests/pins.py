@@ -53,6 +53,78 @@ def _const_frames(n, seed, H=24, W=32, equal_var=False, d0=0.5, spread=2e-3):
 # Alg. 3 and Eq. 9 closed forms
 # ----------------------------------------------------------------------------
 
+def _rule_volume(rule, w, wmax):
+    from dataclasses import replace
+    return replace(_plane_volume(), update_rule=rule, update_weight=w, weight_max=wmax)
+
+
+def _rule_run(rule, w, wmax, n, seed, lib_path):
+    """Static camera, fronto-parallel plane at depth D_k in frame k: every voxel's
+    T_k = D_k - z exactly. Returns (T_k matrix, export, valid-in-all mask,
+    valid-in-some mask)."""
+    vol = _rule_volume(rule, w, wmax)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    D, p, depths, vars_ = _const_frames(n, seed=seed, spread=4e-3)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    _fuse(ov, depths, [np.eye(4)] * n, vars_)
+    e = ov.export()
+    xyz = _voxel_world(vol, oracle.voxel_coords(e))
+    Tk = D[None, :] - xyz[:, 2:3]
+    delta = vol.truncation
+    valid = np.abs(Tk) < delta * (1 - 1e-6)
+    clear = (valid | (np.abs(Tk) > delta * (1 + 1e-6))).all(1) & np.repeat(e.alloc_frame == 0, 512)
+    return Tk, e, valid, clear
+
+
+def pin_alg1_running_average(lib_path=None):
+    """Alg. 1 with a fixed weight w is an exponential moving average: unrolling
+    T_n = (1 - w) T_{n-1} + w T_k(n) from T_1 = T_k(1) gives
+    T_N = (1 - w)^(N-1) T_k(1) + sum_{n=2..N} w (1 - w)^(N-n) T_k(n), over the
+    frames in which the voxel is inside the band (the first of them sets T)."""
+    w, n = 0.375, 8            # weights exactly representable in float32, as the library holds them
+    Tk, e, valid, clear = _rule_run(1, w, 1.0, n, 21, lib_path)
+    T = e.T.ravel()
+    checked = 0
+    for m in (valid.all(1) & clear, valid.any(1) & ~valid.all(1) & clear):
+        rows = np.nonzero(m)[0]
+        exp = np.empty(rows.size)
+        for i, r in enumerate(rows):
+            seq = Tk[r][valid[r]]
+            N = seq.size
+            coef = np.array([(1 - w) ** (N - 1)] + [w * (1 - w) ** (N - k) for k in range(2, N + 1)])
+            exp[i] = (coef * seq).sum()
+        assert np.allclose(T[rows], exp, rtol=0, atol=1e-12), np.abs(T[rows] - exp).max()
+        checked += rows.size
+    assert checked > 5000, checked
+    none = (~valid).all(1) & clear
+    assert none.sum() > 1000 and np.isnan(T[none]).all()
+
+
+def pin_alg2_weighted_average(lib_path=None):
+    """Alg. 2 with a constant weight w: while W + w stays under W_max the result
+    is the plain mean of the measurements and W = (count) w; once W is held at
+    W_max the update becomes T <- a T + (1 - a) T_k with a = W_max / (W_max + w).
+    With W_max = 2.5 w the first three measurements are averaged, and every later
+    one enters with the geometric weight (1 - a) a^(N-n)."""
+    w, n = 0.25, 8             # w and W_max exactly representable in float32
+    Tk, e, valid, clear = _rule_run(2, w, 1e6, n, 22, lib_path)        # W_max never reached
+    m = valid.all(1) & clear
+    assert m.sum() > 5000
+    assert np.allclose(e.T.ravel()[m], Tk[m].mean(1), rtol=0, atol=1e-12)
+    assert np.allclose(e.P.ravel()[m], n * w, rtol=1e-12, atol=0)
+    part = valid.any(1) & ~valid.all(1) & clear
+    assert part.sum() > 1000
+    cnt = valid[part].sum(1)
+    assert np.allclose(e.T.ravel()[part], (Tk[part] * valid[part]).sum(1) / cnt, rtol=0, atol=1e-12)
+    assert np.allclose(e.P.ravel()[part], cnt * w, rtol=1e-12, atol=0)
+    Tk, e, valid, clear = _rule_run(2, w, 2.5 * w, n, 23, lib_path)    # W_max reached at the third
+    m = valid.all(1) & clear
+    a = 2.5 / 3.5
+    exp = a ** (n - 3) * Tk[m][:, :3].mean(1) + sum((1 - a) * a ** (n - k) * Tk[m][:, k - 1] for k in range(4, n + 1))
+    assert np.allclose(e.T.ravel()[m], exp, rtol=0, atol=1e-12), np.abs(e.T.ravel()[m] - exp).max()
+    assert np.allclose(e.P.ravel()[m], 2.5 * w, rtol=1e-12, atol=0)
+
+
 def pin_kalman_closed_form(lib_path=None):
     """With Q = 0, Alg. 3 fed measurements T_k of variances p_k ends at the
     inverse-variance weighted mean: T = sum(T_k/p_k)/sum(1/p_k), P = 1/sum(1/p_k)
@@ -533,6 +605,7 @@ def pin_mlp_variance_fallback(lib_path=None):
 
 
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
+            pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
             pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
             pin_plane_raycast_exact, pin_sphere_raycast_analytic, pin_mlp_gradient_finite_differences,

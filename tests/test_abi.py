@@ -45,6 +45,8 @@ def test_config_defaults(lib):
     assert math.isclose(c.truncation, 7.5e-3, rel_tol=1e-6)
     assert c.grid_dim == 2048 and c.block_capacity == 1 << 20
     assert c.storage == tsdf.STORAGE_F32 and c.alloc_half_samples == 0
+    assert c.update_rule == tsdf.UPDATE_KALMAN
+    assert math.isclose(c.update_weight, 0.1, rel_tol=1e-6) and c.weight_max == 1.0
     assert math.isclose(c.origin[0], -1024 * 1.5e-3, rel_tol=1e-6)
 
 
@@ -63,6 +65,20 @@ def test_status_strings(lib):
 def test_create_rejects_bad_config(lib, field, value):
     c = tsdf.default_config()
     setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert lib.tsdf_create_ex(ctypes.byref(c), ctypes.byref(h)) == tsdf.ERR_INVALID_ARG
+    assert not h.value
+
+
+@pytest.mark.parametrize("rule,weight,wmax", [
+    (3, 0.1, 1.0), (-1, 0.1, 1.0), (tsdf.UPDATE_AVERAGE, 0.0, 1.0), (tsdf.UPDATE_AVERAGE, 1.5, 1.0),
+    (tsdf.UPDATE_AVERAGE, float("nan"), 1.0), (tsdf.UPDATE_WEIGHTED, -1.0, 1.0),
+    (tsdf.UPDATE_WEIGHTED, 2.0, 1.0), (tsdf.UPDATE_WEIGHTED, 0.5, float("inf"))])
+def test_create_rejects_bad_update_rules(lib, rule, weight, wmax):
+    """Alg. 1 needs 0 < w <= 1, Alg. 2 needs w > 0 and a finite W_max >= w
+    (checked on the host, before any device memory is touched)."""
+    c = tsdf.default_config()
+    c.update_rule, c.update_weight, c.weight_max = rule, weight, wmax
     h = ctypes.c_void_p()
     assert lib.tsdf_create_ex(ctypes.byref(c), ctypes.byref(h)) == tsdf.ERR_INVALID_ARG
     assert not h.value

@@ -20,6 +20,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (name, text in the oracle, planted replacement)
 MUTATIONS = [
     ("kalman_correct_sign", "T = T + K * (Tk - T);", "T = T + K * (T - Tk);"),
+    ("alg1_weights_swapped", "T = (1.0 - w) * T + w * Tk;", "T = w * T + (1.0 - w) * Tk;"),
+    ("alg2_no_weight_bound", "W = std::min(W + w, Wmax);", "W = W + w;"),
+    ("alg2_first_weight", "T = Tk;\n        W = w;", "T = Tk;\n        W = 1.0;"),
     ("kalman_variance_shrink", "P = (1.0 - K) * P;", "P = K * P;"),
     ("kalman_predict_sign", "P = P + Q;                    // predict", "P = P - Q;"),
     ("kalman_gain", "const double K = P / (P + pk);", "const double K = pk / (P + pk);"),
