@@ -235,6 +235,30 @@ def render_depth(scene: Scene, intr: Intrinsics, pose: np.ndarray, device="cpu")
     return best
 
 
+def render_maps(scene: Scene, intr: Intrinsics, pose: np.ndarray, device="cpu"):
+    """Exact model maps of the scene seen from ``pose``: camera-z depth (H, W),
+    world vertex and world unit normal (H, W, 3), NaN where the ray misses. The
+    normal is the gradient of the analytic signed distance (central differences
+    of 1e-6 m), turned to face the camera: the maps a perfect raycast of the
+    scene would return."""
+    z = render_depth(scene, intr, pose, device)
+    o, d = _pixel_rays(intr, pose, device)
+    hit = torch.isfinite(z)
+    vert = o + z[..., None] * d
+    eps = 1e-6
+    g = torch.zeros_like(vert)
+    for a in range(3):
+        e = torch.zeros(3, dtype=torch.float64, device=device)
+        e[a] = eps
+        g[..., a] = (scene_sdf(scene, vert + e) - scene_sdf(scene, vert - e)) / (2 * eps)
+    n = g / g.norm(dim=-1, keepdim=True)
+    n = torch.where(((n * d).sum(-1, keepdim=True) > 0), -n, n)
+    nan = torch.full_like(vert, math.nan)
+    vert = torch.where(hit[..., None], vert, nan)
+    n = torch.where(hit[..., None] & torch.isfinite(n), n, nan)
+    return z, vert, n
+
+
 def scene_sdf(scene: Scene, p: torch.Tensor) -> torch.Tensor:
     """Analytic signed distance of the scene union at world points p (..., 3);
     positive outside. Used as ground truth when measuring surface error."""

@@ -604,12 +604,95 @@ def pin_mlp_variance_fallback(lib_path=None):
         assert var[3, 4] == 0.0
 
 
+# ----------------------------------------------------------------------------
+# point-to-plane registration (section "Registration", Eqs. 2-8)
+# ----------------------------------------------------------------------------
+
+def _small_motion(pose, rot_deg, axis, trans):
+    from oracle import icp as oicp
+    a = np.asarray(axis, np.float64)
+    inc = np.eye(4)
+    inc[:3, :3] = oicp.rotation(np.deg2rad(rot_deg) * a / np.linalg.norm(a))
+    inc[:3, 3] = trans
+    return inc @ pose
+
+
+def _room_icp_case(W=160, H=120):
+    seq = synth.room_sequence(n_frames=2, width=W, height=H, device="cpu")
+    model_pose = seq.poses[0]
+    true_pose = _small_motion(model_pose, 1.0, (0.3, 1.0, 0.2), (0.012, -0.008, 0.015))
+    _, mv, mn = synth.render_maps(seq.scene, seq.intr, model_pose)
+    depth = synth.render_depth(seq.scene, seq.intr, true_pose).numpy()
+    depth = np.where(np.isfinite(depth), depth, 0.0).astype(np.float32)
+    return seq.intr, depth, model_pose, true_pose, mv.numpy(), mn.numpy()
+
+
+def pin_icp_recovers_a_known_motion(lib_path=None):
+    """Noise-free frame rendered at a pose 1 degree and 2 cm from the model's:
+    ICP started at the model pose returns the frame's true pose (the whole chain:
+    projective matching, Eq. 4 sums, the unit-cube restatement, Eq. 8 and the
+    pose update). Exact maps of the analytic room stand in for the raycast."""
+    from oracle import icp as oicp
+    intr, depth, model_pose, true_pose, mv, mn = _room_icp_case()
+    pose, info = oicp.icp(depth, intr, model_pose, mv, mn, model_pose, oicp.IcpParams(iterations=12))
+    assert info["matches"] > 10000 and info["rank"] == 6, info
+    dt = np.linalg.norm(pose[:3, 3] - true_pose[:3, 3])
+    ang = np.arccos(np.clip((np.trace(pose[:3, :3] @ true_pose[:3, :3].T) - 1) / 2, -1, 1))
+    # projective matching pairs each frame point with the model point on the
+    # nearest pixel's ray, which leaves a bias far below a pixel's footprint
+    assert dt < 2e-4 and ang < 2e-4, (dt, ang)
+    start = np.linalg.norm(model_pose[:3, 3] - true_pose[:3, 3])
+    assert start > 0.015
+
+
+def pin_icp_scaled_equals_unscaled(lib_path=None):
+    """With no eigen-direction dropped (theta = 0), the unit-cube restatement
+    (Eqs. 5-7) and its recovery give the same motion as solving Eq. 4 directly."""
+    from oracle import icp as oicp
+    intr, depth, model_pose, true_pose, mv, mn = _room_icp_case()
+    p, q, n = oicp.match(depth, intr, model_pose, mv, mn, model_pose, oicp.IcpParams())
+    A, g, _, N = oicp.unscaled_sums(p, q, n)
+    x = np.linalg.solve(A, -g)
+    C, b, m, S = oicp.scaled_system(p, q, n)
+    xh, rank = oicp.solve(C, b, N, 0.0)
+    assert rank == 6
+    r = xh[:3] / S
+    t = xh[3:] - np.cross(r, m)
+    assert np.allclose(r, x[:3], rtol=1e-7, atol=1e-12) and np.allclose(t, x[3:], rtol=1e-7, atol=1e-12)
+    assert np.abs(x).max() > 1e-3     # a real motion, not a trivial zero
+
+
+def pin_icp_plane_keeps_unobservable_motion_out(lib_path=None):
+    """A single plane constrains only the motion along its normal and the tilts:
+    Eq. 8 keeps three eigen-directions and a frame moved within the plane (3 cm
+    along it, 2 degrees about its normal) leaves the pose where it started."""
+    from oracle import icp as oicp
+    scene = synth.Scene(ground_plane=True)
+    intr = synth.Intrinsics.centred(105.0, 160, 120)
+    model_pose = synth.look_at((0.2, 1.2, -0.4), (0.0, 0.0, 0.6))
+    moved = np.eye(4)
+    moved[:3, :3] = oicp.rotation(np.deg2rad(2.0) * np.array([0.0, 1.0, 0.0]))
+    moved[:3, 3] = (0.03, 0.0, 0.01)
+    true_pose = moved @ model_pose
+    _, mv, mn = synth.render_maps(scene, intr, model_pose)
+    depth = synth.render_depth(scene, intr, true_pose).numpy()
+    depth = np.where(np.isfinite(depth), depth, 0.0).astype(np.float32)
+    pose, info = oicp.step(depth, intr, model_pose, mv.numpy(), mn.numpy(), model_pose, oicp.IcpParams())
+    assert info["matches"] > 5000 and info["rank"] == 3, info
+    assert np.abs(pose - model_pose).max() < 1e-6       # float32 depth leaves ~1e-8 m of residual
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
             pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
             pin_plane_raycast_exact, pin_sphere_raycast_analytic, pin_mlp_gradient_finite_differences,
             pin_mlp_closed_forms, pin_mlp_features_on_planes, pin_mlp_variance_fallback]
+
+# the registration oracle is numpy code (oracle/icp.py); its own mutation test
+# plants mistakes in copies of that module
+ICP_PINS = [pin_icp_recovers_a_known_motion, pin_icp_scaled_equals_unscaled,
+            pin_icp_plane_keeps_unobservable_motion_out]
 
 
 def run_all(lib_path=None) -> list:
