@@ -263,6 +263,69 @@ typedef struct {
 tsdf_status tsdf_raycast_trace(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
                                tsdf_raycast_counts* out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Registration (section "Registration", Eqs. 2-8): point-to-plane ICP of a
+ * depth frame against the model maps of tsdf_raycast.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    float dist_max;         /* pairs farther apart than this are rejected, metres (default 0.05) */
+    float normal_cos_min;   /* pairs whose normals' dot product is below this are rejected (default 0.8) */
+    float eig_threshold;    /* theta of Eq. 8: eigen-directions with lambda / pairs <= theta are
+                               dropped (default 0.005) */
+    int32_t iterations;     /* ICP iterations per call, 1..100 (default 10) */
+} tsdf_icp_params;
+
+typedef struct {
+    int64_t matches;        /* accepted pairs in the last iteration */
+    double rms;             /* point-to-plane RMS of those pairs, before that iteration's motion (m) */
+    int32_t rank;           /* eigen-directions kept in the last iteration (6 = fully constrained) */
+    int32_t iterations;     /* iterations run */
+} tsdf_icp_result;
+
+/* Fill *p with the defaults above. Host only. */
+void tsdf_icp_params_default(tsdf_icp_params* p);
+
+/* Register a depth frame to the model: refine *pose_wc (host FP64 4x4 row-major
+ * camera->world; in: initial estimate, out: refined pose) by prm->iterations
+ * iterations of Chen-Medioni point-to-plane ICP. Each iteration back-projects
+ * every frame pixel whose depth and 4-neighbours lie in the volume's
+ * [depth_min, depth_max], takes its normal from the central differences of the
+ * back-projected neighbours, moves both into the world with the current
+ * estimate, matches the point to the model pixel nearest its projection into
+ * the model camera (model_pose_wc), rejects the pair by dist_max and
+ * normal_cos_min, and accumulates the Eq. 4 sums on the GPU (matching,
+ * rejection and the first reduction level in one kernel, the rest in a second,
+ * in double). The host then restates the 6x6 system in the box of the matched
+ * points shrunk to the unit cube (Eqs. 5-7), drops eigen-directions with
+ * lambda / pairs <= theta (Eq. 8), recovers the motion as r = S^-1 r^,
+ * t = t^ - r x m (the scaled unknowns being r^ = S r, t^ = t + r x m), and
+ * applies p -> exp([r]x) p + t to the pose.
+ * depth: device W*H floats of the frame; model_vertex / model_normal: device
+ * W*H*3 floats (world, NaN = no surface) as written by tsdf_raycast with the
+ * same intrinsics K at model_pose_wc. Synchronises with the stream once per
+ * iteration (the pose lives on the host). *out (optional) receives the last
+ * iteration's statistics. An iteration with fewer than 6 pairs leaves the pose
+ * unchanged. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+tsdf_status tsdf_icp(tsdf_volume* vol, const float* depth, const tsdf_intrinsics* K, const float* model_vertex,
+                     const float* model_normal, const double model_pose_wc[16], const tsdf_icp_params* prm,
+                     double pose_wc[16], tsdf_icp_result* out, void* stream);
+
+/* One matching pass of tsdf_icp at pose_wc without solving: the 29 plain sums
+ * of Eq. 4 to host sums[29] (the 21 entries of sum J J^T, upper triangle row
+ * by row, J = (p x n, n); the 6 of sum J ((p - q).n); sum ((p - q).n)^2; the
+ * number of pairs) and the box of the matched points to host box[6] (min x, y,
+ * z, max x, y, z). Synchronous. Errors: as tsdf_icp. */
+tsdf_status tsdf_icp_sums(tsdf_volume* vol, const float* depth, const tsdf_intrinsics* K, const float* model_vertex,
+                          const float* model_normal, const double model_pose_wc[16], const tsdf_icp_params* prm,
+                          const double pose_wc[16], double sums[29], float box[6], void* stream);
+
+/* The host half of one iteration: the motion (r[3] rotation vector, t[3]) from
+ * the sums and box of tsdf_icp_sums and theta (Eqs. 5-8); *rank (optional)
+ * receives the number of eigen-directions kept. Host only, no GPU needed.
+ * Errors: TSDF_ERR_INVALID_ARG (null pointers, theta < 0). */
+tsdf_status tsdf_icp_solve(const double sums[29], const float box[6], float theta, double r[3], double t[3],
+                           int32_t* rank);
+
 /* CUDA-graph driver of the per-step pipeline (no counterpart in the paper; it
  * removes per-kernel launch gaps). A step fuses K frames (1 <= K <= 8) exactly
  * as tsdf_integrate (K = 1) or tsdf_integrate_batch (K > 1) would, then

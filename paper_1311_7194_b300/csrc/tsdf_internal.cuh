@@ -141,6 +141,7 @@ struct tsdf_volume {
     int64_t var_cap;
     float* var_batch;              // [kMaxBatch * var_batch_stride]
     int64_t var_batch_stride;
+    double* icp_part;              // registration partial sums (lazily allocated)
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host
@@ -160,6 +161,11 @@ cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameP
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
 // Raycast with caller-provided near / far range maps (each W*H words).
+cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intrinsics& K, const double pose[16],
+                            const float* mv, const float* mn, const double model_pose[16], const tsdf_icp_params& prm,
+                            double* host_sums, float* host_box, cudaStream_t st);
+int icp_solve(const double* sums, const float* box, double theta, double r[3], double t[3]);
+void icp_apply(const double r[3], const double t[3], double pose[16]);
 cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned char* t_sector, long long n_t,
                                  unsigned char* table_sector, long long n_table, unsigned long long* counts,
                                  cudaStream_t st);

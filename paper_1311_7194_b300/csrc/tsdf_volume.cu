@@ -96,6 +96,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->mlp_w);
     cudaFree(v->var_map);
     cudaFree(v->var_batch);
+    cudaFree(v->icp_part);
 }
 
 }  // namespace
@@ -482,6 +483,66 @@ tsdf_status tsdf_raycast_trace(tsdf_volume* v, const tsdf_intrinsics* K, const d
     out->table_sectors = (int64_t)c[3];
     out->rays = (int64_t)K->width * K->height;
     out->rays_hit = (int64_t)hits;
+    return TSDF_OK;
+}
+
+void tsdf_icp_params_default(tsdf_icp_params* p) {
+    if (!p) return;
+    p->dist_max = 0.05f;
+    p->normal_cos_min = 0.8f;
+    p->eig_threshold = 0.005f;
+    p->iterations = 10;
+}
+
+static bool icp_args_ok(tsdf_volume* v, const float* depth, const tsdf_intrinsics* K, const float* mv,
+                        const float* mn, const double* model_pose, const tsdf_icp_params* prm, const double* pose) {
+    if (!v || !depth || !mv || !mn || !prm || !intr_ok(K) || !pose_ok(model_pose) || !pose_ok(pose)) return false;
+    if (!(std::isfinite(prm->dist_max) && prm->dist_max > 0.0f)) return false;
+    if (!(std::isfinite(prm->normal_cos_min) && prm->normal_cos_min >= -1.0f && prm->normal_cos_min <= 1.0f))
+        return false;
+    if (!(std::isfinite(prm->eig_threshold) && prm->eig_threshold >= 0.0f)) return false;
+    return prm->iterations >= 1 && prm->iterations <= 100;
+}
+
+tsdf_status tsdf_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intrinsics* K, const float* mv,
+                          const float* mn, const double model_pose_wc[16], const tsdf_icp_params* prm,
+                          const double pose_wc[16], double sums[29], float box[6], void* stream) {
+    if (!icp_args_ok(v, depth, K, mv, mn, model_pose_wc, prm, pose_wc) || !sums || !box) return TSDF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    v->last_stream = st;
+    return fail_cuda(v, tsdf::launch_icp_sums(v, depth, *K, pose_wc, mv, mn, model_pose_wc, *prm, sums, box, st));
+}
+
+tsdf_status tsdf_icp_solve(const double sums[29], const float box[6], float theta, double r[3], double t[3],
+                           int32_t* rank) {
+    if (!sums || !box || !r || !t || !(std::isfinite(theta) && theta >= 0.0f)) return TSDF_ERR_INVALID_ARG;
+    const int k = tsdf::icp_solve(sums, box, (double)theta, r, t);
+    if (rank) *rank = k;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_icp(tsdf_volume* v, const float* depth, const tsdf_intrinsics* K, const float* mv, const float* mn,
+                     const double model_pose_wc[16], const tsdf_icp_params* prm, double pose_wc[16],
+                     tsdf_icp_result* out, void* stream) {
+    if (!icp_args_ok(v, depth, K, mv, mn, model_pose_wc, prm, pose_wc)) return TSDF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    v->last_stream = st;
+    tsdf_icp_result res{0, 0.0, 0, 0};
+    for (int it = 0; it < prm->iterations; ++it) {
+        double sums[29];
+        float box[6];
+        const cudaError_t e = tsdf::launch_icp_sums(v, depth, *K, pose_wc, mv, mn, model_pose_wc, *prm, sums, box, st);
+        if (e != cudaSuccess) return fail_cuda(v, e);
+        res.iterations = it + 1;
+        res.matches = (int64_t)sums[28];
+        res.rms = sums[28] > 0.0 ? std::sqrt(sums[27] / sums[28]) : 0.0;
+        res.rank = 0;
+        if (sums[28] < 6.0) continue;
+        double r[3], t[3];
+        res.rank = tsdf::icp_solve(sums, box, (double)prm->eig_threshold, r, t);
+        tsdf::icp_apply(r, t, pose_wc);
+    }
+    if (out) *out = res;
     return TSDF_OK;
 }
 

@@ -437,15 +437,18 @@ def room_sequence(seed: int = 1, n_frames: int = 300, width: int = 640, height: 
                   f: float = 525.0, grid_dim: int = 2048, voxel_size: float = 1.5e-3,
                   block_capacity: int = 1 << 20, noise: bool = True, dropout: float = 0.02,
                   device="cpu", keep_clean: bool = False, origin=None, edge_gain: float = 0.0,
-                  angle_gain: float = 0.0, sigma_coeff: float = 1.5e-3) -> Sequence:
+                  angle_gain: float = 0.0, sigma_coeff: float = 1.5e-3,
+                  trajectory_frames: Optional[int] = None) -> Sequence:
     """Room-scale workload: ground plane + 50 primitives in a 3 m cube, 640x480,
     fx = fy = 525, 300 frames on a seeded spline, sigma = 1.5e-3 z^2, 2 % edge
     dropout, depth range [0.3, 4] m, 2048^3 grid of 1.5 mm voxels (truncation
     5 voxels), pool of 2^20 blocks. Smaller sizes give the reduced parity cases.
     ``edge_gain`` / ``angle_gain`` select a sensor that is also noisier near depth
-    edges and at grazing incidence (the learned-variance workload)."""
+    edges and at grazing incidence (the learned-variance workload).
+    ``trajectory_frames`` > n_frames spreads the closed spline over that many
+    frames and renders the first n_frames (a slower camera)."""
     scene = room_scene(seed)
-    poses = room_trajectory(seed, n_frames)
+    poses = room_trajectory(seed, max(n_frames, trajectory_frames or n_frames))[:n_frames]
     if origin is None:
         origin = (-0.036, -0.036, -0.036)
     vol = VolumeParams(voxel_size=voxel_size, truncation=5 * voxel_size, origin=tuple(origin),

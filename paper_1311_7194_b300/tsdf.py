@@ -23,7 +23,8 @@ UPDATE_KALMAN, UPDATE_AVERAGE, UPDATE_WEIGHTED = 0, 1, 2      # tsdf_update_rule
 # Every function the header declares (checked against include/tsdf.h by the tests).
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
-            "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
+            "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_icp_params_default", "tsdf_icp", "tsdf_icp_sums",
+            "tsdf_icp_solve", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
             "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
             "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
             "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
@@ -74,6 +75,20 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class IcpParams(ctypes.Structure):
+    _fields_ = [("dist_max", ctypes.c_float), ("normal_cos_min", ctypes.c_float), ("eig_threshold", ctypes.c_float),
+                ("iterations", ctypes.c_int32)]
+
+
+class IcpResult(ctypes.Structure):
+    _fields_ = [("matches", ctypes.c_int64), ("rms", ctypes.c_double), ("rank", ctypes.c_int32),
+                ("iterations", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"matches": int(self.matches), "rms": float(self.rms), "rank": int(self.rank),
+                "iterations": int(self.iterations)}
+
+
 class RaycastCounts(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int64), ("table_lookups", ctypes.c_int64), ("t_sectors", ctypes.c_int64),
                 ("table_sectors", ctypes.c_int64), ("rays", ctypes.c_int64), ("rays_hit", ctypes.c_int64)]
@@ -112,6 +127,13 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_raycast_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
         "tsdf_raycast_trace": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, ctypes.POINTER(RaycastCounts),
                                               _P]),
+        "tsdf_icp_params_default": (None, [ctypes.POINTER(IcpParams)]),
+        "tsdf_icp": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _P, _P, _PD, ctypes.POINTER(IcpParams), _PD,
+                                    ctypes.POINTER(IcpResult), _P]),
+        "tsdf_icp_sums": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _P, _P, _PD, ctypes.POINTER(IcpParams),
+                                         _PD, _PD, ctypes.POINTER(ctypes.c_float), _P]),
+        "tsdf_icp_solve": (ctypes.c_int, [_PD, ctypes.POINTER(ctypes.c_float), ctypes.c_float, _PD, _PD,
+                                          ctypes.POINTER(ctypes.c_int32)]),
         "tsdf_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Intrinsics), ctypes.POINTER(_P)]),
         "tsdf_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
         "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
@@ -180,6 +202,26 @@ def config_from(vol, **overrides) -> Config:
     for k, v in overrides.items():
         setattr(c, k, v)
     return c
+
+
+def icp_params(**kw) -> IcpParams:
+    """tsdf_icp_params with the library defaults, fields overridden by ``kw``."""
+    p = IcpParams()
+    load().tsdf_icp_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def icp_solve(sums, box, theta: float = 0.005):
+    """tsdf_icp_solve (host only): (r, t, rank) from Eq. 4 sums and the box."""
+    s = (ctypes.c_double * 29)(*[float(x) for x in np.asarray(sums, np.float64).ravel()])
+    b = (ctypes.c_float * 6)(*[float(x) for x in np.asarray(box, np.float32).ravel()])
+    r = (ctypes.c_double * 3)()
+    t = (ctypes.c_double * 3)()
+    k = ctypes.c_int32()
+    _check(load().tsdf_icp_solve(s, b, float(theta), r, t, ctypes.byref(k)), "tsdf_icp_solve")
+    return np.array(r[:]), np.array(t[:]), int(k.value)
 
 
 def intrinsics(intr) -> Intrinsics:
@@ -323,6 +365,35 @@ class Volume:
         _check(self.lib.tsdf_raycast_trace(self.h, ctypes.byref(K), _pose(pose), ctypes.byref(c), _stream(stream)),
                "tsdf_raycast_trace")
         return c.as_dict()
+
+    def icp(self, depth, intr, model_vertex, model_normal, model_pose, pose0, params=None, stream=None):
+        """tsdf_icp: refine ``pose0`` (4x4 camera -> world) by registering the
+        frame ``depth`` (H, W) to the model maps (H, W, 3 world vertex / normal,
+        from a raycast at ``model_pose``). Returns (pose, statistics)."""
+        K = intrinsics(intr)
+        n = K.width * K.height
+        prm = icp_params(**(params or {}))
+        pose = _pose(pose0)
+        res = IcpResult()
+        _check(self.lib.tsdf_icp(self.h, _dev_ptr(depth, n, "depth"), ctypes.byref(K),
+                                 _dev_ptr(model_vertex, 3 * n, "model_vertex"),
+                                 _dev_ptr(model_normal, 3 * n, "model_normal"), _pose(model_pose), ctypes.byref(prm),
+                                 pose, ctypes.byref(res), _stream(stream)), "tsdf_icp")
+        return np.array(pose[:], np.float64).reshape(4, 4), res.as_dict()
+
+    def icp_sums(self, depth, intr, model_vertex, model_normal, model_pose, pose, params=None, stream=None):
+        """tsdf_icp_sums: the 29 plain Eq. 4 sums and the matched box of one
+        matching pass at ``pose``."""
+        K = intrinsics(intr)
+        n = K.width * K.height
+        prm = icp_params(**(params or {}))
+        sums = (ctypes.c_double * 29)()
+        box = (ctypes.c_float * 6)()
+        _check(self.lib.tsdf_icp_sums(self.h, _dev_ptr(depth, n, "depth"), ctypes.byref(K),
+                                      _dev_ptr(model_vertex, 3 * n, "model_vertex"),
+                                      _dev_ptr(model_normal, 3 * n, "model_normal"), _pose(model_pose),
+                                      ctypes.byref(prm), _pose(pose), sums, box, _stream(stream)), "tsdf_icp_sums")
+        return np.array(sums[:]), np.array(box[:], np.float32)
 
     def launch_config(self) -> dict:
         c = LaunchConfig()
