@@ -9,7 +9,8 @@
 //                      reject by distance and normal deviation, and accumulate
 //                      the Eq. 4 sums (J J^T, J r with J = (p x n, n), r =
 //                      (p - q).n), sum r^2, the count and the box of the
-//                      matched points; per CTA in double.
+//                      matched points; lanes in float, a CTA's warps in
+//                      double.
 //   icp_final_kernel:  the CTAs' partial sums in a fixed order, in double.
 // The paper does matching, rejection and the first reduction level in one
 // kernel and the further levels in another; so does this file. The 6x6 solve
@@ -141,11 +142,14 @@ __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(IcpFrame f, con
             hi[a] = fmaxf(hi[a], fmaxf(p[a], q[a]));
         }
     }
+    // FP64 arithmetic is scarce on this GPU: the 32 lanes' sums are formed in
+    // float (a few pixels each) and only the warps' sums are added in double
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kSums; ++k) {
-        const double s = warp_sum_d((double)acc[k]);
-        if (lane == 0) ssum[warp][k] = s;
+        float s = acc[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) ssum[warp][k] = (double)s;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -172,20 +176,46 @@ __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(IcpFrame f, con
     }
 }
 
-// One CTA: thread k < kSums adds the CTAs' partial k in CTA order (the same
-// order every run); threads 32..37 reduce the box.
-__global__ void __launch_bounds__(64) icp_final_kernel(const double* __restrict__ part,
-                                                       const float* __restrict__ pbox, int n_parts,
-                                                       double* __restrict__ out, float* __restrict__ box) {
-    if (threadIdx.x < kSums) {
+// kSums + 1 CTAs: CTA k < kSums adds the CTAs' partial k (thread j taking CTAs
+// j, j + 256, ..., then a fixed shuffle tree and the warps in order: the same
+// order every run); the last CTA reduces the box.
+__global__ void __launch_bounds__(kIcpThreads) icp_final_kernel(const double* __restrict__ part,
+                                                                const float* __restrict__ pbox, int n_parts,
+                                                                double* __restrict__ out, float* __restrict__ box) {
+    __shared__ double sw[kIcpThreads / 32];
+    __shared__ float sb[kIcpThreads / 32][6];
+    const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (k < kSums) {
         double s = 0.0;
-        for (int b = 0; b < n_parts; ++b) s += part[(size_t)b * kSums + threadIdx.x];
-        out[threadIdx.x] = s;
-    } else if (threadIdx.x >= 32 && threadIdx.x < 38) {
-        const int a = threadIdx.x - 32;
-        float v = a < 3 ? 3.0e38f : -3.0e38f;
-        for (int b = 0; b < n_parts; ++b) v = a < 3 ? fminf(v, pbox[(size_t)b * 6 + a]) : fmaxf(v, pbox[(size_t)b * 6 + a]);
-        box[a] = v;
+        for (int b = threadIdx.x; b < n_parts; b += kIcpThreads) s += part[(size_t)b * kSums + k];
+        s = warp_sum_d(s);
+        if (lane == 0) sw[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kIcpThreads / 32; ++w) t += sw[w];
+            out[k] = t;
+        }
+    } else {
+        float v[6] = {3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
+        for (int b = threadIdx.x; b < n_parts; b += kIcpThreads)
+            for (int a = 0; a < 6; ++a)
+                v[a] = a < 3 ? fminf(v[a], pbox[(size_t)b * 6 + a]) : fmaxf(v[a], pbox[(size_t)b * 6 + a]);
+        for (int a = 0; a < 6; ++a) {
+            float x = v[a];
+            for (int o = 16; o > 0; o >>= 1) {
+                const float y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = a < 3 ? fminf(x, y) : fmaxf(x, y);
+            }
+            if (lane == 0) sb[warp][a] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int a = threadIdx.x;
+            float x = sb[0][a];
+            for (int w = 1; w < kIcpThreads / 32; ++w) x = a < 3 ? fminf(x, sb[w][a]) : fmaxf(x, sb[w][a]);
+            box[a] = x;
+        }
     }
 }
 
@@ -354,7 +384,7 @@ cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intri
     f.cos_min = prm.normal_cos_min;
     f.depth_min = v->cfg.depth_min;
     f.depth_max = v->cfg.depth_max;
-    const int grid = v->num_sms * 2;
+    const int grid = v->num_sms * 4;
     if (!v->icp_part) {
         cudaError_t e = cudaMalloc(&v->icp_part, (size_t)grid * (kSums + 3) * sizeof(double) + 64 * sizeof(double));
         if (e != cudaSuccess) return e;
@@ -364,7 +394,7 @@ cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intri
     double* out = part + (size_t)grid * (kSums + 3);                              // kSums doubles
     float* box = reinterpret_cast<float*>(out + kSums + 1);                       // 6 floats
     icp_reduce_kernel<<<grid, kIcpThreads, 0, st>>>(f, depth, mv, mn, part, pbox);
-    icp_final_kernel<<<1, 64, 0, st>>>(part, pbox, grid, out, box);
+    icp_final_kernel<<<kSums + 1, kIcpThreads, 0, st>>>(part, pbox, grid, out, box);
     cudaError_t e = cudaMemcpyAsync(host_sums, out, kSums * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_box, box, 6 * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
