@@ -56,7 +56,8 @@ class _Params(ctypes.Structure):
                 ("sigma_coeff", ctypes.c_float), ("alloc_half_samples", ctypes.c_int32),
                 ("amb_px", ctypes.c_double), ("amb_trunc", ctypes.c_double),
                 ("store_values", ctypes.c_int32), ("update_rule", ctypes.c_int32),
-                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float)]
+                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float),
+                ("refine_steps", ctypes.c_int32)]
 
 
 class _Intr(ctypes.Structure):
@@ -139,6 +140,7 @@ def make_params(vol, amb_px: float = 1e-3, amb_trunc: float = 1e-5, store_values
     p.update_rule = int(getattr(vol, "update_rule", 0))
     p.update_weight = float(getattr(vol, "update_weight", 0.1))
     p.weight_max = float(getattr(vol, "weight_max", 1.0))
+    p.refine_steps = int(getattr(vol, "refine_steps", 0))
     return p
 
 

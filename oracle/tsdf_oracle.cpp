@@ -27,6 +27,8 @@
 //   * Alg. 2 (weighted scene TSDF estimation): T <- (W T + w_k T_k) / (W + w_k),
 //     W <- min(W + w_k, W_max), chi if |T| > delta; the weight W is kept where
 //     Alg. 3 keeps P.
+//   * Section "Integration of Measurements", last paragraph: optionally, T_k
+//     refined by gradient (Gauss-Newton) steps in the depth map (refine_tk).
 //   * Eq. 9: averaging N measurements of deviation sigma leaves variance sigma^2/N
 //     (used by the tests as a closed-form pin).
 //   * Section "Scene Rendering": the depth/normal map of the fused surface is found
@@ -72,6 +74,7 @@ struct ov_params {
                                 // 2 = Alg. 2 (weighted average with W_max)
     float update_weight;        // w_k of Alg. 1 / Alg. 2 (the same for every measurement)
     float weight_max;           // W_max of Alg. 2
+    int32_t refine_steps;       // Gauss-Newton steps refining T_k in the depth map (0 = off)
 };
 
 struct ov_intr {
@@ -304,6 +307,86 @@ PixMeas pixel_measure(const ov_params& p, const Frame& f, double u, double v, do
     return m;
 }
 
+// Section "Integration of Measurements", last paragraph: a finer T_k by a few
+// gradient steps in the depth map towards the local minimum of the distance
+// between the measured surface and x. Reading: the measured surface is the
+// depth map back-projected, S(u, v) = D~(u, v) ((u - cx)/fx, (v - cy)/fy, 1),
+// with D~ the bilinear interpolation of the four pixels around (u, v); the
+// steps are Gauss-Newton steps on |S(u, v) - X|^2 from the voxel's projection;
+// an evaluation needs all four pixels valid and within delta of each other (no
+// depth edge). T_k is the distance |S - X| at the last valid evaluation, signed
+// by the side of S's tangent plane X lies on (positive on the camera side:
+// outside, Eq. 1), or stays the z-difference when no evaluation is valid. *amb is set when an evaluation point lies within amb_px
+// of a pixel-cell line, where float rounding could pick another cell.
+struct SurfEval {
+    bool ok;
+    double S[3], Ju[3], Jv[3];
+};
+
+SurfEval surface_eval(const ov_params& p, const Frame& f, double u, double v) {
+    SurfEval e{false, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double fi = std::floor(u), fj = std::floor(v);
+    if (!(fi >= 0.0 && fj >= 0.0 && fi + 1.0 < (double)f.in.width && fj + 1.0 < (double)f.in.height)) return e;
+    const int64_t i = (int64_t)fi, j = (int64_t)fj, W = f.in.width;
+    const float d00 = f.depth[j * W + i], d10 = f.depth[j * W + i + 1];
+    const float d01 = f.depth[(j + 1) * W + i], d11 = f.depth[(j + 1) * W + i + 1];
+    if (!(depth_valid(d00, p) && depth_valid(d10, p) && depth_valid(d01, p) && depth_valid(d11, p))) return e;
+    const double D00 = d00, D10 = d10, D01 = d01, D11 = d11;
+    const double lo = std::min(std::min(D00, D10), std::min(D01, D11));
+    const double hi = std::max(std::max(D00, D10), std::max(D01, D11));
+    if (hi - lo > (double)p.truncation) return e;
+    const double a = u - fi, b = v - fj;
+    const double D = (1 - a) * (1 - b) * D00 + a * (1 - b) * D10 + (1 - a) * b * D01 + a * b * D11;
+    const double Du = (1 - b) * (D10 - D00) + b * (D11 - D01);
+    const double Dv = (1 - a) * (D01 - D00) + a * (D11 - D10);
+    const double fx = f.in.fx, fy = f.in.fy;
+    const double ray[3] = {(u - (double)f.in.cx) / fx, (v - (double)f.in.cy) / fy, 1.0};
+    for (int k = 0; k < 3; ++k) {
+        e.S[k] = D * ray[k];
+        e.Ju[k] = Du * ray[k];
+        e.Jv[k] = Dv * ray[k];
+    }
+    e.Ju[0] += D / fx;
+    e.Jv[1] += D / fy;
+    e.ok = true;
+    return e;
+}
+
+bool near_cell_line(double x, double margin) {
+    const double r = x - std::floor(x);
+    return r < margin || 1.0 - r < margin;
+}
+
+double refine_tk(const ov_params& p, const Frame& f, const double X[3], double uf, double vf, double Tk0,
+                 bool* amb) {
+    double u = uf, v = vf, dist = -1.0, side = 1.0;
+    for (int k = 0; k <= p.refine_steps; ++k) {
+        if (near_cell_line(u, p.amb_px) || near_cell_line(v, p.amb_px)) *amb = true;
+        const SurfEval e = surface_eval(p, f, u, v);
+        if (!e.ok) break;
+        const double r[3] = {e.S[0] - X[0], e.S[1] - X[1], e.S[2] - X[2]};
+        dist = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        // tangent-plane normal Ju x Jv turned to the camera (at the origin)
+        double n[3] = {e.Ju[1] * e.Jv[2] - e.Ju[2] * e.Jv[1], e.Ju[2] * e.Jv[0] - e.Ju[0] * e.Jv[2],
+                       e.Ju[0] * e.Jv[1] - e.Ju[1] * e.Jv[0]};
+        if (n[0] * e.S[0] + n[1] * e.S[1] + n[2] * e.S[2] > 0.0)
+            for (double& c : n) c = -c;
+        side = (-r[0] * n[0] - r[1] * n[1] - r[2] * n[2]) >= 0.0 ? 1.0 : -1.0;   // (X - S).n
+        if (k == p.refine_steps) break;
+        const double a11 = e.Ju[0] * e.Ju[0] + e.Ju[1] * e.Ju[1] + e.Ju[2] * e.Ju[2];
+        const double a12 = e.Ju[0] * e.Jv[0] + e.Ju[1] * e.Jv[1] + e.Ju[2] * e.Jv[2];
+        const double a22 = e.Jv[0] * e.Jv[0] + e.Jv[1] * e.Jv[1] + e.Jv[2] * e.Jv[2];
+        const double g1 = e.Ju[0] * r[0] + e.Ju[1] * r[1] + e.Ju[2] * r[2];
+        const double g2 = e.Jv[0] * r[0] + e.Jv[1] * r[1] + e.Jv[2] * r[2];
+        const double det = a11 * a22 - a12 * a12;
+        if (!(det > 0.0)) break;
+        u -= (a22 * g1 - a12 * g2) / det;
+        v -= (a11 * g2 - a12 * g1) / det;
+    }
+    if (dist < 0.0) return Tk0;
+    return side * dist;
+}
+
 Meas measure(const ov_params& p, const Frame& f, int64_t ix, int64_t iy, int64_t iz) {
     Meas m{false, false, 0.0, 0.0};
     const double s = (double)p.voxel_size;
@@ -336,6 +419,7 @@ Meas measure(const ov_params& p, const Frame& f, int64_t ix, int64_t iy, int64_t
             mc.trunc_amb)
             m.amb = true;
     }
+    if (m.valid && p.refine_steps > 0) m.Tk = refine_tk(p, f, xc, uf, vf, m.Tk, &m.amb);
     return m;
 }
 

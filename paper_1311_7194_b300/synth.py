@@ -68,6 +68,7 @@ class VolumeParams:
     update_rule: int = 0        # 0 Alg. 3 (Kalman), 1 Alg. 1 (running average), 2 Alg. 2 (weighted)
     update_weight: float = 0.1  # w_k of Alg. 1 / Alg. 2
     weight_max: float = 1.0     # W_max of Alg. 2
+    refine_steps: int = 0       # Gauss-Newton steps refining T_k in the depth map (0 = off)
 
 
 @dataclass

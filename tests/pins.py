@@ -682,12 +682,86 @@ def pin_icp_plane_keeps_unobservable_motion_out(lib_path=None):
     assert np.abs(pose - model_pose).max() < 1e-6       # float32 depth leaves ~1e-8 m of residual
 
 
+# ----------------------------------------------------------------------------
+# T_k refined by gradient steps in the depth map (section "Integration of
+# Measurements", last paragraph)
+# ----------------------------------------------------------------------------
+
+def _refined_single_frame(depth, intr, steps, lib_path, s=2e-3, G=128, z_centre=0.6):
+    from dataclasses import replace
+    vol = replace(_plane_volume(s=s, G=G, z_centre=z_centre, sigma=1e-3, cap=1 << 14), refine_steps=steps)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    ov.fuse(depth, np.eye(4))
+    e = ov.export()
+    xyz = _voxel_world(vol, oracle.voxel_coords(e))
+    T = e.T.ravel()
+    ok = ~np.isnan(T) & ~e.amb.ravel()
+    return vol, xyz[ok], T[ok]
+
+
+def pin_refined_tk_plane_distances(lib_path=None):
+    """Gauss-Newton steps move to the foot of the perpendicular: for a
+    fronto-parallel plane the refined T_k is the z-difference itself; for a plane
+    tilted by 35 degrees it is the signed perpendicular distance
+    d0 cos(theta) - n.X, smaller than the z-difference by cos(theta)."""
+    W, H, f = 96, 72, 90.0
+    intr = synth.Intrinsics.centred(f, W, H)
+    d0 = 0.6
+    flat = np.full((H, W), d0, np.float32)
+    vol, X, T = _refined_single_frame(flat, intr, 3, lib_path)
+    assert T.size > 5000
+    assert np.abs(T - (float(np.float32(d0)) - X[:, 2])).max() < 1e-9
+    th = np.deg2rad(35.0)
+    v, u = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    yn = (v - intr.cy) / intr.fx
+    tilt = (d0 * np.cos(th) / (np.cos(th) - np.sin(th) * yn)).astype(np.float32)
+    vol, X, T = _refined_single_frame(tilt, intr, 3, lib_path)
+    n = np.array([0.0, -np.sin(th), np.cos(th)])
+    exact = d0 * np.cos(th) - X @ n
+    zdiff_scale = np.abs(exact).max() / np.cos(th)
+    assert T.size > 5000 and zdiff_scale > 0.5 * vol.truncation
+    err = np.abs(T - exact)
+    assert np.percentile(err, 99) < 1e-3 * vol.truncation and err.max() < 1e-2 * vol.truncation, err.max()
+
+
+def pin_refined_tk_sphere_distance(lib_path=None):
+    """Near a sphere the refined T_k approaches the Euclidean distance |X - c| - r
+    (up to the bilinear interpolation of the depth map), which the plain
+    z-difference overestimates away from the centre of the view."""
+    W, H, f = 96, 72, 90.0
+    intr = synth.Intrinsics.centred(f, W, H)
+    c, r = np.array([0.01, -0.02, 0.6]), 0.12
+    scene = synth.Scene(spheres=np.array([[c[0], c[1], c[2], r]]))
+    depth = synth.render_depth(scene, intr, np.eye(4)).numpy()
+    depth = np.where(np.isfinite(depth), depth, 0.0).astype(np.float32)
+    vol, X, T = _refined_single_frame(depth, intr, 3, lib_path, z_centre=0.55)
+    _, X0, T0 = _refined_single_frame(depth, intr, 0, lib_path, z_centre=0.55)
+    # voxels whose viewing ray passes within 0.7 r of the centre: there
+    # neighbouring pixels differ by less than delta, so the steps apply (nearer
+    # the silhouette the depth map has edges and T_k stays the z-difference); and
+    # beyond 0.45 r, where the surface is oblique enough for the z-difference to
+    # overestimate the distance
+    def ring(P):
+        ray = P / np.linalg.norm(P, axis=1, keepdims=True)
+        miss = np.linalg.norm(np.cross(ray, c[None, :]), axis=1)      # distance of the ray from c
+        return (miss > 0.45 * r) & (miss < 0.7 * r)
+    exact = np.linalg.norm(X - c, axis=1) - r
+    m = ring(X)
+    assert m.sum() > 2000
+    err = np.abs(T - exact)[m]
+    assert np.percentile(err, 99) < 0.02 * vol.truncation, np.percentile(err, 99)
+    m0 = ring(X0)
+    err0 = np.abs(T0 - (np.linalg.norm(X0 - c, axis=1) - r))[m0]
+    assert np.median(err0) > 10 * np.median(err), (np.median(err0), np.median(err))
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
             pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
             pin_plane_raycast_exact, pin_sphere_raycast_analytic, pin_mlp_gradient_finite_differences,
-            pin_mlp_closed_forms, pin_mlp_features_on_planes, pin_mlp_variance_fallback]
+            pin_mlp_closed_forms, pin_mlp_features_on_planes, pin_mlp_variance_fallback,
+            pin_refined_tk_plane_distances, pin_refined_tk_sphere_distance]
 
 # the registration oracle is numpy code (oracle/icp.py); its own mutation test
 # plants mistakes in copies of that module

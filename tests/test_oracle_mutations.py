@@ -20,6 +20,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (name, text in the oracle, planted replacement)
 MUTATIONS = [
     ("kalman_correct_sign", "T = T + K * (Tk - T);", "T = T + K * (T - Tk);"),
+    ("refine_step_sign", "u -= (a22 * g1 - a12 * g2) / det;", "u += (a22 * g1 - a12 * g2) / det;"),
+    ("refine_jacobian_scale", "e.Ju[0] += D / fx;", "e.Ju[0] += D;"),
+    ("refine_side_unoriented", "side = (-r[0] * n[0] - r[1] * n[1] - r[2] * n[2]) >= 0.0 ? 1.0 : -1.0;",
+     "side = 1.0;"),
     ("alg1_weights_swapped", "T = (1.0 - w) * T + w * Tk;", "T = w * T + (1.0 - w) * Tk;"),
     ("alg2_no_weight_bound", "W = std::min(W + w, Wmax);", "W = W + w;"),
     ("alg2_first_weight", "T = Tk;\n        W = w;", "T = Tk;\n        W = 1.0;"),
