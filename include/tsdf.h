@@ -101,6 +101,12 @@ typedef struct {
     float update_weight;        /* w_k of Alg. 1 (0 < w <= 1) and Alg. 2 (w > 0),
                                    the same for every measurement (default 0.1) */
     float weight_max;           /* W_max >= w of Alg. 2 (default 1) */
+    int32_t refine_steps;       /* 0..8 Gauss-Newton steps refining T_k in the depth map
+                                   (section "Integration of Measurements", last paragraph):
+                                   T_k becomes the distance from the voxel to the bilinear
+                                   back-projected depth surface, signed by its tangent plane,
+                                   wherever the four pixels around each step are valid and
+                                   within delta of each other (default 0 = the z-difference) */
 } tsdf_config;
 
 /* Counters of the last calls (tsdf_get_stats). */

@@ -331,10 +331,12 @@ SurfEval surface_eval(const ov_params& p, const Frame& f, double u, double v) {
     const float d00 = f.depth[j * W + i], d10 = f.depth[j * W + i + 1];
     const float d01 = f.depth[(j + 1) * W + i], d11 = f.depth[(j + 1) * W + i + 1];
     if (!(depth_valid(d00, p) && depth_valid(d10, p) && depth_valid(d01, p) && depth_valid(d11, p))) return e;
+    // the depth-edge test is a branch decided by float values: it is taken in
+    // float32, as the library takes it
+    const float lo32 = std::min(std::min(d00, d10), std::min(d01, d11));
+    const float hi32 = std::max(std::max(d00, d10), std::max(d01, d11));
+    if (hi32 - lo32 > p.truncation) return e;
     const double D00 = d00, D10 = d10, D01 = d01, D11 = d11;
-    const double lo = std::min(std::min(D00, D10), std::min(D01, D11));
-    const double hi = std::max(std::max(D00, D10), std::max(D01, D11));
-    if (hi - lo > (double)p.truncation) return e;
     const double a = u - fi, b = v - fj;
     const double D = (1 - a) * (1 - b) * D00 + a * (1 - b) * D10 + (1 - a) * b * D01 + a * b * D11;
     const double Du = (1 - b) * (D10 - D00) + b * (D11 - D01);
@@ -419,7 +421,12 @@ Meas measure(const ov_params& p, const Frame& f, int64_t ix, int64_t iy, int64_t
             mc.trunc_amb)
             m.amb = true;
     }
-    if (m.valid && p.refine_steps > 0) m.Tk = refine_tk(p, f, xc, uf, vf, m.Tk, &m.amb);
+    if (m.valid && p.refine_steps > 0) {
+        m.Tk = refine_tk(p, f, xc, uf, vf, m.Tk, &m.amb);
+        // a refined T_k near +-delta makes the chi test after the update a close call
+        const double delta = (double)p.truncation;
+        if (std::fabs(std::fabs(m.Tk) - delta) <= p.amb_trunc * delta) m.amb = true;
+    }
     return m;
 }
 

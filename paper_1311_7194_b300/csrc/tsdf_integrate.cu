@@ -248,7 +248,58 @@ __device__ __forceinline__ float rcp_newton(float x) {
 // distance to the measured point; chi when there is no measurement). The voxel
 // is lx steps along the block's x rows from a row start whose camera position
 // is (xr, yr, o_z + zr); zr carries the low part of o_z.
-template <bool kVarMap>
+// T_k refined by Gauss-Newton steps in the depth map (section "Integration of
+// Measurements", last paragraph): the measured surface is the depth map
+// back-projected with bilinear depth, S(u, v) = D~(u, v) ((u - cx)/fx,
+// (v - cy)/fy, 1); steps on |S - X|^2 start at the voxel's projection (u, v);
+// an evaluation needs the four pixels valid and within delta of each other.
+// T_k is |S - X| at the last valid evaluation, signed by the side of S's
+// tangent plane X lies on (camera side positive), or t0 (the z-difference)
+// when no evaluation is valid. X = (x, y, zh + zl): the z part is kept as a
+// hi/lo pair so that S_z - X_z = (D~ - zh) - zl keeps full precision.
+__device__ __forceinline__ float refine_tk(const FrameParams& p, const float* __restrict__ depth, float x, float y,
+                                           float zh, float zl, float u, float v, float t0) {
+    float dist = -1.0f, side = 1.0f;
+    for (int k = 0; k <= p.refine_steps; ++k) {
+        const float fi = floorf(u), fj = floorf(v);
+        if (!(fi >= 0.0f && fj >= 0.0f && fi + 1.0f < (float)p.width && fj + 1.0f < (float)p.height)) break;
+        const int i = (int)fi, j = (int)fj;
+        const float* row = depth + (size_t)j * p.width + i;
+        const float d00 = __ldg(row), d10 = __ldg(row + 1), d01 = __ldg(row + p.width), d11 = __ldg(row + p.width + 1);
+        if (!(depth_ok(d00, p.depth_min, p.depth_max) && depth_ok(d10, p.depth_min, p.depth_max) &&
+              depth_ok(d01, p.depth_min, p.depth_max) && depth_ok(d11, p.depth_min, p.depth_max)))
+            break;
+        if (fmaxf(fmaxf(d00, d10), fmaxf(d01, d11)) - fminf(fminf(d00, d10), fminf(d01, d11)) > p.delta) break;
+        const float a = u - fi, b = v - fj;
+        const float D = (1.0f - a) * (1.0f - b) * d00 + a * (1.0f - b) * d10 + (1.0f - a) * b * d01 + a * b * d11;
+        const float Du = (1.0f - b) * (d10 - d00) + b * (d11 - d01);
+        const float Dv = (1.0f - a) * (d01 - d00) + a * (d11 - d10);
+        const float rx_ = (u - p.cx) / p.fx, ry_ = (v - p.cy) / p.fy;
+        const float S[3] = {D * rx_, D * ry_, D};
+        const float Ju[3] = {Du * rx_ + D / p.fx, Du * ry_, Du};
+        const float Jv[3] = {Dv * rx_, Dv * ry_ + D / p.fy, Dv};
+        const float r[3] = {S[0] - x, S[1] - y, (D - zh) - zl};
+        dist = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        float n[3] = {Ju[1] * Jv[2] - Ju[2] * Jv[1], Ju[2] * Jv[0] - Ju[0] * Jv[2], Ju[0] * Jv[1] - Ju[1] * Jv[0]};
+        if (n[0] * S[0] + n[1] * S[1] + n[2] * S[2] > 0.0f) {
+            n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+        }
+        side = (-r[0] * n[0] - r[1] * n[1] - r[2] * n[2]) >= 0.0f ? 1.0f : -1.0f;
+        if (k == p.refine_steps) break;
+        const float a11 = Ju[0] * Ju[0] + Ju[1] * Ju[1] + Ju[2] * Ju[2];
+        const float a12 = Ju[0] * Jv[0] + Ju[1] * Jv[1] + Ju[2] * Jv[2];
+        const float a22 = Jv[0] * Jv[0] + Jv[1] * Jv[1] + Jv[2] * Jv[2];
+        const float g1 = Ju[0] * r[0] + Ju[1] * r[1] + Ju[2] * r[2];
+        const float g2 = Jv[0] * r[0] + Jv[1] * r[1] + Jv[2] * r[2];
+        const float det = a11 * a22 - a12 * a12;
+        if (!(det > 0.0f)) break;
+        u -= (a22 * g1 - a12 * g2) / det;
+        v -= (a11 * g2 - a12 * g1) / det;
+    }
+    return dist < 0.0f ? t0 : side * dist;
+}
+
+template <bool kVarMap, bool kRefine>
 __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
                                         float zr, const float* __restrict__ depth, const float* __restrict__ var,
                                         float* Tk, float* pk) {
@@ -275,7 +326,7 @@ __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock
         pv = __fmul_rn(sg, sg);
     }
     if (!(pv > 0.0f && pv <= 3.0e38f)) return false;
-    *Tk = t;
+    *Tk = kRefine ? refine_tk(p, depth, x, y, vb.o[2], zs, uf - 0.5f, vf - 0.5f, t) : t;
     *pk = pv;
     return true;
 }
@@ -308,7 +359,7 @@ __device__ __forceinline__ void update(const FrameParams& p, float& T, float& P,
     if (fabsf(T) > p.delta) T = __int_as_float(0x7fc00000);
 }
 
-template <bool kVarMap, int kS, int kVPT, int kRule>
+template <bool kVarMap, int kS, int kVPT, int kRule, bool kRefine>
 __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters* __restrict__ ctr,
                                                                         const VisibleBlock* __restrict__ vis,
                                                                         typename Codec<kS>::E* __restrict__ T,
@@ -331,7 +382,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters
         bool any = false;
 #pragma unroll
         for (int e = 0; e < kVPT; ++e) {
-            ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
+            ok[e] = measure<kVarMap, kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
             any |= ok[e];
         }
         if (!any) continue;
@@ -367,7 +418,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters
 // before the block's allocation - and stored once. Same measurement and update
 // functions as integrate_kernel, so the result equals K sequential calls bit
 // for bit.
-template <bool kVarMap, int kS, int kRule>
+template <bool kVarMap, int kS, int kRule, bool kRefine>
 __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
                                                                             const VisibleBlock* __restrict__ vis,
                                                                             const int4* __restrict__ blocks,
@@ -395,7 +446,8 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             bool any = false;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                ok[e] = measure<kVarMap>(p, vb, lx0 + (float)e, xr, yr, zr, bp.depth[k], bp.var[k], &tk[e], &pk[e]);
+                ok[e] = measure<kVarMap, kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, bp.depth[k], bp.var[k], &tk[e],
+                                                  &pk[e]);
                 any |= ok[e];
             }
             if (!any) continue;
@@ -431,15 +483,27 @@ __global__ void reset_frame_counters(Counters* ctr) {
     ctr->voxel_updates = 0;
 }
 
-template <int kS, int kVPT, int kRule>
-void launch_integrate_r(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+template <int kS, int kVPT, int kRule, bool kRefine>
+void launch_integrate_f(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
                         cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     constexpr int threads = kBlockVoxels / kVPT;
     if (var)
-        integrate_kernel<true, kS, kVPT, kRule><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+        integrate_kernel<true, kS, kVPT, kRule, kRefine><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth,
+                                                                                 var, p);
     else
-        integrate_kernel<false, kS, kVPT, kRule><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth, var, p);
+        integrate_kernel<false, kS, kVPT, kRule, kRefine><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P,
+                                                                                  depth, var, p);
+}
+
+// The refined measurement is instantiated for 4 voxels per thread only.
+template <int kS, int kVPT, int kRule>
+void launch_integrate_r(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
+                        cudaStream_t st) {
+    if (p.refine_steps > 0)
+        launch_integrate_f<kS, 4, kRule, true>(v, depth, var, p, grid, st);
+    else
+        launch_integrate_f<kS, kVPT, kRule, false>(v, depth, var, p, grid, st);
 }
 
 template <int kS, int kVPT>
@@ -461,15 +525,23 @@ void launch_integrate_s(tsdf_volume* v, const float* depth, const float* var, co
         launch_integrate_v<kS, 4>(v, depth, var, p, grid, st);
 }
 
-template <int kS, int kRule>
-void launch_integrate_batch_r(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
+template <int kS, int kRule, bool kRefine>
+void launch_integrate_batch_f(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     if (bp.var[0])
-        integrate_batch_kernel<true, kS, kRule><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch,
-                                                                                    v->blocks, T, v->P, bp);
+        integrate_batch_kernel<true, kS, kRule, kRefine><<<grid, kIntegrateThreads, 0, st>>>(
+            v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
     else
-        integrate_batch_kernel<false, kS, kRule><<<grid, kIntegrateThreads, 0, st>>>(v->ctr, v->visible_batch,
-                                                                                     v->blocks, T, v->P, bp);
+        integrate_batch_kernel<false, kS, kRule, kRefine><<<grid, kIntegrateThreads, 0, st>>>(
+            v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
+}
+
+template <int kS, int kRule>
+void launch_integrate_batch_r(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
+    if (bp.fp[0].refine_steps > 0)
+        launch_integrate_batch_f<kS, kRule, true>(v, bp, grid, st);
+    else
+        launch_integrate_batch_f<kS, kRule, false>(v, bp, grid, st);
 }
 
 template <int kS>

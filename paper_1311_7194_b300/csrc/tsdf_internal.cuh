@@ -82,6 +82,7 @@ struct FrameParams {
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;
     float w, wmax;       // w_k and W_max of Alg. 1 / Alg. 2 (the rule itself is a kernel template argument)
+    int refine_steps;    // Gauss-Newton steps refining T_k in the depth map (0 = off)
     float2 tsc;          // snorm16 scales: (delta / 32767, 32767 / delta)
     float zlo, zhi;      // camera z range a block must reach to matter
     float near_clip, far_clip;

@@ -151,6 +151,7 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.sigma_coeff = v->cfg.sigma_coeff;
     p.w = v->cfg.update_weight;
     p.wmax = v->cfg.weight_max;
+    p.refine_steps = v->cfg.refine_steps;
     p.tsc = make_float2((float)((double)v->cfg.truncation / 32767.0), (float)(32767.0 / (double)v->cfg.truncation));
     const double dl = 1.01 * (double)v->cfg.truncation;
     p.zlo = (float)((double)v->cfg.depth_min - dl);
@@ -254,6 +255,7 @@ void tsdf_config_default(tsdf_config* c) {
     c->update_rule = TSDF_UPDATE_KALMAN;
     c->update_weight = 0.1f;
     c->weight_max = 1.0f;
+    c->refine_steps = 0;
 }
 
 const char* tsdf_status_string(tsdf_status s) {
@@ -288,6 +290,7 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
         return TSDF_ERR_INVALID_ARG;
     if (c.alloc_half_samples < 0 || c.alloc_half_samples > 4096) return TSDF_ERR_INVALID_ARG;
     if (c.update_rule < TSDF_UPDATE_KALMAN || c.update_rule > TSDF_UPDATE_WEIGHTED) return TSDF_ERR_INVALID_ARG;
+    if (c.refine_steps < 0 || c.refine_steps > 8) return TSDF_ERR_INVALID_ARG;
     if (c.update_rule != TSDF_UPDATE_KALMAN) {
         if (!(std::isfinite(c.update_weight) && c.update_weight > 0.0f)) return TSDF_ERR_INVALID_ARG;
         if (c.update_rule == TSDF_UPDATE_AVERAGE && !(c.update_weight <= 1.0f)) return TSDF_ERR_INVALID_ARG;

@@ -46,7 +46,8 @@ class Config(ctypes.Structure):
                 ("raycast_near", ctypes.c_float), ("raycast_far", ctypes.c_float),
                 ("sigma_coeff", ctypes.c_float), ("storage", ctypes.c_int32),
                 ("alloc_half_samples", ctypes.c_int32), ("update_rule", ctypes.c_int32),
-                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float)]
+                ("update_weight", ctypes.c_float), ("weight_max", ctypes.c_float),
+                ("refine_steps", ctypes.c_int32)]
 
 
 class Intrinsics(ctypes.Structure):
@@ -199,6 +200,7 @@ def config_from(vol, **overrides) -> Config:
     c.update_rule = int(getattr(vol, "update_rule", UPDATE_KALMAN))
     c.update_weight = float(getattr(vol, "update_weight", c.update_weight))
     c.weight_max = float(getattr(vol, "weight_max", c.weight_max))
+    c.refine_steps = int(getattr(vol, "refine_steps", 0))
     for k, v in overrides.items():
         setattr(c, k, v)
     return c

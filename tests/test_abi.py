@@ -47,6 +47,7 @@ def test_config_defaults(lib):
     assert c.storage == tsdf.STORAGE_F32 and c.alloc_half_samples == 0
     assert c.update_rule == tsdf.UPDATE_KALMAN
     assert math.isclose(c.update_weight, 0.1, rel_tol=1e-6) and c.weight_max == 1.0
+    assert c.refine_steps == 0
     assert math.isclose(c.origin[0], -1024 * 1.5e-3, rel_tol=1e-6)
 
 
@@ -61,7 +62,7 @@ def test_status_strings(lib):
     ("grid_dim", 100), ("grid_dim", 0), ("grid_dim", 8 * 1700), ("block_capacity", 0),
     ("block_capacity", 1 << 40), ("process_variance", -1.0), ("sigma_coeff", float("inf")),
     ("depth_max", 0.05), ("raycast_near", 0.0), ("raycast_far", 0.01), ("storage", 7),
-    ("alloc_half_samples", -1)])
+    ("alloc_half_samples", -1), ("refine_steps", -1), ("refine_steps", 9)])
 def test_create_rejects_bad_config(lib, field, value):
     c = tsdf.default_config()
     setattr(c, field, value)

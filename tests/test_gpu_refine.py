@@ -1,0 +1,81 @@
+"""T_k refined by Gauss-Newton steps in the depth map (tsdf_config.refine_steps,
+section "Integration of Measurements", last paragraph) against the FP64 oracle,
+K-batched equal to sequential, and its effect on the fused surface."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_1311_7194_b300 import learned_variance as lv
+from paper_1311_7194_b300 import synth, tsdf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1311_7194_b300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def test_refined_tk_matches_oracle():
+    seq = synth.with_volume(synth.room_sequence(n_frames=8, width=157, height=117, grid_dim=512, voxel_size=6e-3,
+                                                block_capacity=1 << 16), refine_steps=3)
+    vol = tsdf.Volume.from_params(seq.volume)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, amb_px=5e-4)
+    for k in range(seq.n_frames):
+        vol.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k])
+        ov.fuse(seq.depth[k], seq.poses[k])
+    nb = seq.volume.grid_dim // 8
+    ge, oe = vol.export(), ov.export()
+    r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
+    assert r["keys_equal"] and r["frames_equal"], r
+    _, _, gT, gP = compare.sort_by_key(ge.coords, ge.alloc_frame, ge.T, ge.P, nb)
+    # the lateral camera coordinates enter |S - X| in float (no hi/lo split), a
+    # few 1e-7 m at 2 m, and three float Gauss-Newton steps stop a little apart
+    # from the double ones: 2e-4 delta (6 um here) rather than 1e-5
+    v = compare.compare_values(gT, gP, oe.T, oe.P, oe.amb, seq.volume.truncation, tol_T=2e-4)
+    assert v["ok"], json.dumps(v)
+    assert v["compared"] > 100000 and v["ambiguous_valid_frac"] < 0.2, json.dumps(v)
+
+
+def test_refined_tk_batched_equals_sequential():
+    seq = synth.with_volume(synth.sphere_sequence(n_frames=8), refine_steps=2)
+    a = tsdf.Volume.from_params(seq.volume)
+    for k in range(seq.n_frames):
+        a.fuse(_cuda(seq.depth[k]), seq.intr, seq.poses[k])
+    b = tsdf.Volume.from_params(seq.volume)
+    b.integrate_batch([_cuda(seq.depth[k]) for k in range(8)], seq.intr, seq.poses[:8])
+    ea, eb = a.export(), b.export()
+    chi = np.isnan(ea.T)
+    assert np.array_equal(chi, np.isnan(eb.T))
+    assert np.array_equal(ea.T.view(np.uint32)[~chi], eb.T.view(np.uint32)[~chi])
+    assert np.array_equal(ea.P.view(np.uint32)[~chi], eb.P.view(np.uint32)[~chi])
+
+
+def test_refined_tk_surface_error():
+    """Room scene at 320x240 on a 1024^3 grid of 3 mm voxels: the fused surface
+    measured by the analytic distance at the raycast vertices, with the plain
+    z-difference and with three refinement steps."""
+    seq = synth.room_sequence(seed=1, n_frames=40, width=320, height=240, grid_dim=1024, voxel_size=3e-3,
+                              block_capacity=1 << 18, device="cuda")
+    poses = [seq.poses[k] for k in (10, 20, 30)]
+    out = {}
+    for steps in (0, 3):
+        vol = tsdf.Volume.from_params(seq.volume, refine_steps=steps)
+        d = torch.from_numpy(seq.depth).cuda()
+        for k in range(seq.n_frames):
+            vol.fuse(d[k], seq.intr, seq.poses[k])
+        out[steps] = lv.surface_error(vol, seq, poses, seq.scene)
+    print(f"surface error: z-difference {json.dumps(out[0])}, refined {json.dumps(out[3])}")
+    assert out[3]["mae"] <= 1.05 * out[0]["mae"]
+    assert abs(out[3]["hits"] - out[0]["hits"]) < 0.02 * out[0]["hits"]
