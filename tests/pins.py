@@ -755,6 +755,65 @@ def pin_refined_tk_sphere_distance(lib_path=None):
     assert np.median(err0) > 10 * np.median(err), (np.median(err0), np.median(err))
 
 
+# ----------------------------------------------------------------------------
+# marching-cubes surface (section "Scene Rendering", the polygonising renderer)
+# ----------------------------------------------------------------------------
+
+def _edge_use(tris):
+    """Directed mesh edges (vertex keys rounded to 1e-9) and their counts."""
+    from collections import Counter
+    key = lambda p: tuple(np.round(p, 9))
+    d = Counter()
+    for t in tris:
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            d[(key(t[a]), key(t[b]))] += 1
+    return d
+
+
+def pin_mesh_sphere_closed_and_outward(lib_path=None):
+    """The exact signed distance of a sphere sampled on a lattice gives a closed,
+    consistently oriented surface: every directed edge appears once and its
+    reverse once, V - E + F = 2, vertices lie on the sphere within the linear
+    interpolation error, and every triangle's normal points outward."""
+    from oracle import mesh as omesh
+    s, n, r = 1.0, 24, 7.3
+    c = np.array([11.2, 12.1, 11.7])
+    g = np.indices((n, n, n)).transpose(1, 2, 3, 0).astype(np.float64)
+    T = np.linalg.norm(g - c, axis=-1) - r
+    tris = omesh.mesh(T, (0.0, 0.0, 0.0), s)
+    assert tris.shape[0] > 500
+    use = _edge_use(tris)
+    assert all(v == 1 for v in use.values())
+    assert all(use.get((b, a), 0) == 1 for (a, b) in use)
+    V = len({p for e in use for p in e})
+    E = len(use) // 2
+    assert V - E + tris.shape[0] == 2
+    d = np.abs(np.linalg.norm(tris - c, axis=-1) - r)
+    assert d.max() < 0.05 * s, d.max()
+    nrm = np.cross(tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0])
+    assert (np.einsum("ij,ij->i", nrm, tris.mean(1) - c) > 0).all()
+
+
+def pin_mesh_every_case_closed(lib_path=None):
+    """Each of the 256 corner sign patterns, embedded in a lattice with a
+    one-voxel margin of positive values, gives a closed oriented surface (all
+    directed edges paired), and every crossed edge lies on exactly one loop."""
+    from oracle import mesh as omesh
+    for case in range(1, 255):
+        T = np.ones((4, 4, 4))
+        for cidx in range(8):
+            if case >> cidx & 1:
+                T[1 + (cidx & 1), 1 + ((cidx >> 1) & 1), 1 + ((cidx >> 2) & 1)] = -1.0
+        tris = omesh.mesh(T, (0.0, 0.0, 0.0), 1.0)
+        use = _edge_use(tris)
+        assert all(v == 1 and use.get((b, a), 0) == 1 for (a, b), v in use.items()), case
+    for case in range(256):
+        # every crossed edge of the cell is on exactly one loop
+        ins = tuple(bool(case >> k & 1) for k in range(8))
+        crossed = sorted(k for k, (a, b) in enumerate(omesh.EDGES) if ins[a] != ins[b])
+        assert sorted(e for l in omesh.case_polygons(ins) for e in l) == crossed, case
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
@@ -767,6 +826,7 @@ ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_st
 # plants mistakes in copies of that module
 ICP_PINS = [pin_icp_recovers_a_known_motion, pin_icp_scaled_equals_unscaled,
             pin_icp_plane_keeps_unobservable_motion_out]
+MESH_PINS = [pin_mesh_sphere_closed_and_outward, pin_mesh_every_case_closed]
 
 
 def run_all(lib_path=None) -> list:

@@ -4,6 +4,6 @@ import pytest
 import pins
 
 
-@pytest.mark.parametrize("pin", pins.ALL_PINS + pins.ICP_PINS, ids=lambda f: f.__name__)
+@pytest.mark.parametrize("pin", pins.ALL_PINS + pins.ICP_PINS + pins.MESH_PINS, ids=lambda f: f.__name__)
 def test_pin(oracle_lib, pin):
     pin()
