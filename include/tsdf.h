@@ -269,6 +269,31 @@ typedef struct {
 tsdf_status tsdf_raycast_trace(tsdf_volume* vol, const tsdf_intrinsics* K, const double pose_wc[16],
                                tsdf_raycast_counts* out, void* stream);
 
+/* Marching-cubes surface of the volume (section "Scene Rendering": the
+ * paper's polygonising renderer). Every cell - the cube of lattice voxels
+ * i + {0,1}^3 - whose 8 voxels are defined (allocated, not chi) is polygonised:
+ * a corner is inside when T < 0, the surface crosses an edge at the linear
+ * zero of T, and the cell's triangles come from a case table the library
+ * builds from the published construction (per-face segments, a face with four
+ * crossings pairing each inside corner's two edges, segments oriented so the
+ * normal points from inside to outside, loops fan-split from their smallest
+ * edge number), which keeps the surface closed across cells. Output:
+ * triangles as 9 floats each (three world xyz vertices, counter-clockwise seen
+ * from outside), ordered by pool slot and, within a block, by cell
+ * (x fastest). Call with triangles = NULL to get the count in *n_triangles
+ * (host), then with a device buffer of max_triangles >= that count; a smaller
+ * buffer gets TSDF_ERR_CAPACITY and nothing written. Synchronous. Errors:
+ * TSDF_ERR_INVALID_ARG, TSDF_ERR_CAPACITY, TSDF_ERR_CUDA. */
+tsdf_status tsdf_mesh(tsdf_volume* vol, float* triangles, int64_t max_triangles, int64_t* n_triangles,
+                      void* stream);
+
+/* The case table entry for a corner pattern (bit c set = corner c inside,
+ * corners c = x + 2y + 4z): *n_triangles and their edges, 3 per triangle, in
+ * edges[24] (edges 0-3 run along x from corners 0, 2, 4, 6; 4-7 along y from
+ * corners 0, 1, 4, 5; 8-11 along z from corners 0, 1, 2, 3). Host only.
+ * Errors: TSDF_ERR_INVALID_ARG. */
+tsdf_status tsdf_mesh_case(int32_t pattern, int32_t* n_triangles, int8_t edges[24]);
+
 /* ---------------------------------------------------------------------------
  * Registration (section "Registration", Eqs. 2-8): point-to-plane ICP of a
  * depth frame against the model maps of tsdf_raycast.

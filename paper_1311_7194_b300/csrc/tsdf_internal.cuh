@@ -143,6 +143,8 @@ struct tsdf_volume {
     float* var_batch;              // [kMaxBatch * var_batch_stride]
     int64_t var_batch_stride;
     double* icp_part;              // registration partial sums (lazily allocated)
+    void* mesh_scratch;            // marching cubes: per-block counts and offsets (lazily allocated)
+    int mesh_table_ready;          // the case table is in constant memory
     int64_t frame;                 // host copy of the frame counter
     cudaStream_t last_stream;
     tsdf_status host_error;        // sticky CUDA error seen on the host
@@ -167,6 +169,8 @@ cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intri
                             double* host_sums, float* host_box, cudaStream_t st);
 int icp_solve(const double* sums, const float* box, double theta, double r[3], double t[3]);
 void icp_apply(const double r[3], const double t[3], double pose[16]);
+cudaError_t launch_mesh(tsdf_volume* v, float* out, bool emit, long long* n, cudaStream_t st);
+int mesh_case(int cs, signed char* edges);
 cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned char* t_sector, long long n_t,
                                  unsigned char* table_sector, long long n_table, unsigned long long* counts,
                                  cudaStream_t st);

@@ -97,6 +97,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->var_map);
     cudaFree(v->var_batch);
     cudaFree(v->icp_part);
+    cudaFree(v->mesh_scratch);
 }
 
 }  // namespace
@@ -486,6 +487,30 @@ tsdf_status tsdf_raycast_trace(tsdf_volume* v, const tsdf_intrinsics* K, const d
     out->table_sectors = (int64_t)c[3];
     out->rays = (int64_t)K->width * K->height;
     out->rays_hit = (int64_t)hits;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_mesh(tsdf_volume* v, float* triangles, int64_t max_triangles, int64_t* n_triangles,
+                      void* stream) {
+    if (!v || !n_triangles || max_triangles < 0 || (triangles && max_triangles == 0)) return TSDF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    v->last_stream = st;
+    long long n = 0;
+    cudaError_t e = tsdf::launch_mesh(v, nullptr, false, &n, st);
+    if (e != cudaSuccess) return fail_cuda(v, e);
+    *n_triangles = (int64_t)n;
+    if (!triangles) return TSDF_OK;
+    if (n > max_triangles) return TSDF_ERR_CAPACITY;
+    e = tsdf::launch_mesh(v, triangles, true, &n, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? TSDF_OK : fail_cuda(v, e);
+}
+
+tsdf_status tsdf_mesh_case(int32_t pattern, int32_t* n_triangles, int8_t edges[24]) {
+    if (pattern < 0 || pattern > 255 || !n_triangles || !edges) return TSDF_ERR_INVALID_ARG;
+    signed char e[24];
+    *n_triangles = tsdf::mesh_case(pattern, e);
+    for (int k = 0; k < 24; ++k) edges[k] = (int8_t)e[k];
     return TSDF_OK;
 }
 

@@ -24,7 +24,7 @@ UPDATE_KALMAN, UPDATE_AVERAGE, UPDATE_WEIGHTED = 0, 1, 2      # tsdf_update_rule
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
             "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_icp_params_default", "tsdf_icp", "tsdf_icp_sums",
-            "tsdf_icp_solve", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
+            "tsdf_icp_solve", "tsdf_mesh", "tsdf_mesh_case", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
             "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
             "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
             "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
@@ -128,6 +128,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_raycast_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, _P, _P, _P, _P]),
         "tsdf_raycast_trace": (ctypes.c_int, [_P, ctypes.POINTER(Intrinsics), _PD, ctypes.POINTER(RaycastCounts),
                                               _P]),
+        "tsdf_mesh": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
+        "tsdf_mesh_case": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int8)]),
         "tsdf_icp_params_default": (None, [ctypes.POINTER(IcpParams)]),
         "tsdf_icp": (ctypes.c_int, [_P, _P, ctypes.POINTER(Intrinsics), _P, _P, _PD, ctypes.POINTER(IcpParams), _PD,
                                     ctypes.POINTER(IcpResult), _P]),
@@ -204,6 +207,15 @@ def config_from(vol, **overrides) -> Config:
     for k, v in overrides.items():
         setattr(c, k, v)
     return c
+
+
+def mesh_case(pattern: int):
+    """tsdf_mesh_case (host only): the triangles (edge-number triples) of a
+    corner pattern."""
+    n = ctypes.c_int32()
+    e = (ctypes.c_int8 * 24)()
+    _check(load().tsdf_mesh_case(int(pattern), ctypes.byref(n), e), "tsdf_mesh_case")
+    return [tuple(e[3 * k:3 * k + 3]) for k in range(n.value)]
 
 
 def icp_params(**kw) -> IcpParams:
@@ -367,6 +379,19 @@ class Volume:
         _check(self.lib.tsdf_raycast_trace(self.h, ctypes.byref(K), _pose(pose), ctypes.byref(c), _stream(stream)),
                "tsdf_raycast_trace")
         return c.as_dict()
+
+    def mesh(self, stream=None):
+        """tsdf_mesh: the marching-cubes surface as an (n, 3, 3) float32 device
+        tensor of world-space triangles."""
+        import torch
+        n = ctypes.c_int64(0)
+        _check(self.lib.tsdf_mesh(self.h, None, 0, ctypes.byref(n), _stream(stream)), "tsdf_mesh")
+        out = torch.empty((max(int(n.value), 1), 3, 3), dtype=torch.float32,
+                          device=torch.device("cuda", torch.cuda.current_device()))
+        if n.value:
+            _check(self.lib.tsdf_mesh(self.h, ctypes.c_void_p(out.data_ptr()), int(n.value), ctypes.byref(n),
+                                      _stream(stream)), "tsdf_mesh")
+        return out[:int(n.value)]
 
     def icp(self, depth, intr, model_vertex, model_normal, model_pose, pose0, params=None, stream=None):
         """tsdf_icp: refine ``pose0`` (4x4 camera -> world) by registering the
