@@ -58,11 +58,12 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=0,
                     help="capsules: compare this many sampled voxels with the FP64 oracle (per-voxel replay)")
     ap.add_argument("--icp-iterations", type=int, default=6, help="tracking: ICP iterations per frame")
-    ap.add_argument("--workload", choices=["room", "batched", "capsules", "sphere", "tracking"], default="room",
+    ap.add_argument("--workload", choices=["room", "batched", "capsules", "sphere", "tracking", "mesh"],
+                    default="room",
                     help="room: per-frame live fusion (2048^3, 1.5 mm); batched: 3000^3 grid of 1 mm voxels, "
                          "1000 frames fused K=8 per graph launch, raycast per batch; capsules: 1280x1024 "
                          "small objects on a 4096^3 grid of 0.15 mm voxels; sphere: the 160x120 parity scene; "
-                         "tracking: raycast -> ICP -> fuse at the registered pose")
+                         "tracking: raycast -> ICP -> fuse at the registered pose; mesh: marching-cubes extraction")
     ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
     ap.add_argument("--cpu-ray-stride", type=int, default=8, help="oracle sample: pixel stride per axis")
     return ap.parse_args()
@@ -668,6 +669,62 @@ def run_tracking(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mesh(args):
+    """Marching-cubes extraction (tsdf_mesh) of the room volume after fusing
+    the 300-frame sequence (640x480, 2048^3 grid of 1.5 mm voxels): one step =
+    count + emit of the whole surface; triangles/s and ms per extraction, next
+    to the raycast of one view of the same volume (the paper compares its two
+    renderers)."""
+    import numpy as np
+    import torch
+
+    from paper_1311_7194_b300 import build as pkg_build
+    from paper_1311_7194_b300 import tsdf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pkg_build.build()
+    seq = make_sequence(args.frames, dev, args.block_capacity)
+    F, H, W = seq.depth.shape
+    d = torch.from_numpy(seq.depth).to(dev)
+    vol = tsdf.Volume.from_params(seq.volume)
+    vol.set_launch_config(raycast_persistent=1)
+    for k in range(F):
+        vol.fuse(d[k], seq.intr, seq.poses[k])
+    torch.cuda.synchronize()
+    tri = None
+    for _ in range(max(args.warmup, 0)):
+        tri = vol.mesh()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tri = vol.mesh()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    maps = (torch.empty((H, W), device=dev), torch.empty((H, W, 3), device=dev), torch.empty((H, W, 3), device=dev))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        vol.raycast(seq.intr, seq.poses[-1], out=maps)
+    e0.record()
+    for _ in range(20):
+        vol.raycast(seq.intr, seq.poses[-1], out=maps)
+    e1.record()
+    torch.cuda.synchronize()
+    n = int(tri.shape[0])
+    st = vol.stats()
+    line = {"metric": "triangles/s", "value": n / sec, "unit": "triangles/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"marching-cubes extraction of the room volume after {F} frames (2048^3 grid of "
+                                   "1.5 mm voxels), count + emit, wall clock (synchronous call)",
+                       "blocks": int(st["n_blocks"]), "triangles": n},
+            "raycast_ms_one_view": e0.elapsed_time(e1) / 20, "clocks": clk}
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -680,6 +737,8 @@ def main():
         run_capsules(args)
     elif args.workload == "tracking":
         run_tracking(args)
+    elif args.workload == "mesh":
+        run_mesh(args)
     else:
         run_ours(args)
 
