@@ -256,6 +256,14 @@ typedef struct {
     int64_t table_sectors;  /* distinct 32-byte sectors of the block table read */
     int64_t rays;           /* W * H */
     int64_t rays_hit;
+    /* by phase (samples = march_samples + rescan_samples + refine_samples
+     * + normal_samples) */
+    int64_t march_samples;  /* coarse march iterations (each takes one sample) */
+    int64_t skips;          /* of those, samples in an unallocated block: an empty-space jump */
+    int64_t rescans;        /* re-scans of a step that entered the field at or below zero */
+    int64_t rescan_samples; /* samples those re-scans took */
+    int64_t refine_samples; /* false-position samples of the crossing refinement */
+    int64_t normal_samples; /* central-difference samples of the normals */
 } tsdf_raycast_counts;
 
 /* Run the raycast of tsdf_raycast at pose_wc with every sample traced and

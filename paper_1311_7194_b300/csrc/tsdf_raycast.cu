@@ -185,6 +185,14 @@ __device__ __forceinline__ void trace_corner(int slot, int off) {
     g_trace.t_sector[byte >> 5] = 1;
 }
 
+// counts[4..9]: march samples, empty-space skips, re-scans, re-scan samples,
+// refinement samples, normal samples
+enum { kTraceMarch = 4, kTraceSkip, kTraceRescan, kTraceRescanSample, kTraceRefineSample, kTraceNormalSample };
+template <bool kTrace>
+__device__ __forceinline__ void trace_add(int i, unsigned long long n = 1) {
+    if (kTrace) atomicAdd(&g_trace.counts[i], n);
+}
+
 __device__ __forceinline__ void trace_lookup(const FrameParams& p, int bx, int by, int bz) {
     const unsigned long long e = (unsigned)bx + (unsigned long long)p.nb * ((unsigned)by + (unsigned long long)p.nb * (unsigned)bz);
     g_trace.table_sector[e >> 3] = 1;
@@ -329,9 +337,11 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
             float zprev_any = z, zstep = h;   // last sample taken and the step since
             int blk[3];
             for (int it = 0; it < kMaxMarch && z <= zend; ++it) {
+                trace_add<kTrace>(kTraceMarch);
                 const int st = trilinear<kS, kTrace>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
                                          __fmaf_rn(z, dqz, p.q0[2]), &f, blk);
                 if (st == 2) {
+                    trace_add<kTrace>(kTraceSkip);
                     // everything before the empty cell's exit is undefined
                     zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
                     z = zprev_any + 1e-3f * h;
@@ -347,8 +357,10 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                     bool ldef = false, stop = false;
                     float fl = 0.0f, zl = 0.0f;
                     const float back = fminf(zstep, z - zprev_any);
+                    trace_add<kTrace>(kTraceRescan);
                     for (int j = 0; j <= kFine; ++j) {
                         const float zq = j == kFine ? z : z - back + (float)j * (back / (float)kFine);
+                        if (j < kFine) trace_add<kTrace>(kTraceRescanSample);
                         float fq = f;
                         const int sq = j == kFine ? 0
                                                   : trilinear<kS, kTrace>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
@@ -399,6 +411,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                 zs = z1 + (z2 - z1) * (f1 / (f1 - f2));
                 for (int r = 0; r < kRefine && z2 - z1 > eps; ++r) {
                     float fs;
+                    trace_add<kTrace>(kTraceRefineSample);
                     if (trilinear<kS, kTrace>(p, table, T, __fmaf_rn(zs, dqx, p.q0[0]), __fmaf_rn(zs, dqy, p.q0[1]),
                                   __fmaf_rn(zs, dqz, p.q0[2]), &fs, blk) != 0)
                         break;
@@ -418,11 +431,17 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                             qz = __fmaf_rn(zs, dqz, p.q0[2]);
                 float fp[3], fm[3];
                 bool ok = true;
+                trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx + 1.0f, qy, qz, &fp[0], blk) == 0;
+                if (ok) trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx - 1.0f, qy, qz, &fm[0], blk) == 0;
+                if (ok) trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy + 1.0f, qz, &fp[1], blk) == 0;
+                if (ok) trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy - 1.0f, qz, &fm[1], blk) == 0;
+                if (ok) trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy, qz + 1.0f, &fp[2], blk) == 0;
+                if (ok) trace_add<kTrace>(kTraceNormalSample);
                 ok = ok && trilinear<kS, kTrace>(p, table, T, qx, qy, qz - 1.0f, &fm[2], blk) == 0;
                 if (ok) {
                     float g[3] = {fp[0] - fm[0], fp[1] - fm[1], fp[2] - fm[2]};

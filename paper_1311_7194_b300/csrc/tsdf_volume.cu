@@ -467,12 +467,12 @@ tsdf_status tsdf_raycast_trace(tsdf_volume* v, const tsdf_intrinsics* K, const d
     unsigned long long* counts = nullptr;
     cudaError_t e = cudaMalloc(&t_sector, (size_t)n_t);
     if (e == cudaSuccess) e = cudaMalloc(&table_sector, (size_t)n_table);
-    if (e == cudaSuccess) e = cudaMalloc(&counts, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&counts, 10 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(t_sector, 0, (size_t)n_t, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(table_sector, 0, (size_t)n_table, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 10 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = tsdf::launch_raycast_trace(v, p, t_sector, n_t, table_sector, n_table, counts, st);
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long hits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(c, counts, sizeof(c), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hits, &v->ctr->rays_hit, sizeof(hits), cudaMemcpyDeviceToHost, st);
@@ -487,6 +487,12 @@ tsdf_status tsdf_raycast_trace(tsdf_volume* v, const tsdf_intrinsics* K, const d
     out->table_sectors = (int64_t)c[3];
     out->rays = (int64_t)K->width * K->height;
     out->rays_hit = (int64_t)hits;
+    out->march_samples = (int64_t)c[4];
+    out->skips = (int64_t)c[5];
+    out->rescans = (int64_t)c[6];
+    out->rescan_samples = (int64_t)c[7];
+    out->refine_samples = (int64_t)c[8];
+    out->normal_samples = (int64_t)c[9];
     return TSDF_OK;
 }
 

@@ -92,7 +92,10 @@ class IcpResult(ctypes.Structure):
 
 class RaycastCounts(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int64), ("table_lookups", ctypes.c_int64), ("t_sectors", ctypes.c_int64),
-                ("table_sectors", ctypes.c_int64), ("rays", ctypes.c_int64), ("rays_hit", ctypes.c_int64)]
+                ("table_sectors", ctypes.c_int64), ("rays", ctypes.c_int64), ("rays_hit", ctypes.c_int64),
+                ("march_samples", ctypes.c_int64), ("skips", ctypes.c_int64), ("rescans", ctypes.c_int64),
+                ("rescan_samples", ctypes.c_int64), ("refine_samples", ctypes.c_int64),
+                ("normal_samples", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

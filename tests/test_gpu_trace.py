@@ -43,3 +43,9 @@ def test_trace_counts_are_consistent(storage):
     assert c["t_sectors"] <= 8 * c["samples"]
     assert 0 < c["table_sectors"] <= c["table_lookups"]
     assert c["table_sectors"] <= (512 // 8) ** 3 // 8
+    # the phase counts add up to the samples taken
+    assert c["samples"] == c["march_samples"] + c["rescan_samples"] + c["refine_samples"] + c["normal_samples"]
+    assert c["normal_samples"] <= 6 * c["rays_hit"]
+    assert c["rescan_samples"] <= 16 * c["rescans"]
+    assert c["refine_samples"] <= 10 * c["rays_hit"]
+    assert c["march_samples"] >= c["rays_hit"] and c["skips"] <= c["march_samples"]
