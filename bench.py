@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "room-scale plain FP32: 640x480, 2048^3 grid of 1.5 mm voxels, 300 frames"
 METRIC, UNIT = "frames/s", "frames/s"
-LAUNCHES_PER_FRAME = 14    # allocate 5 + integrate 4 + raycast 5 kernels
+LAUNCHES_PER_FRAME = 12    # allocate 5 + integrate 3 + raycast 4 kernels
 
 
 def parse():

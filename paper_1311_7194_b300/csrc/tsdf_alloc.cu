@@ -28,6 +28,7 @@ constexpr unsigned kNoKey = 0xffffffffu;
 __global__ void __launch_bounds__(256) alloc_mark_kernel(const float* __restrict__ depth, AllocParams p,
                                                          const int* __restrict__ blk_slot,
                                                          unsigned int* __restrict__ newbits) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     const long long n = (long long)p.width * p.height;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,6 +94,7 @@ __device__ __forceinline__ unsigned block_sum(unsigned x, unsigned* smem) {
 
 __global__ void __launch_bounds__(kTileThreads) alloc_count_kernel(const uint4* __restrict__ words,
                                                                    unsigned int* __restrict__ tile_sums) {
+    pdl_prologue();
     __shared__ unsigned smem[32];
     const uint4* base = words + (size_t)blockIdx.x * (kTileWords / 4);
     unsigned c = 0;
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
                                                                     int4* __restrict__ blocks, long long cap,
                                                                     int frame, int nb, unsigned int* __restrict__ occ2,
                                                                     unsigned int* __restrict__ occ3, int n2, int n3) {
+    pdl_prologue();
     __shared__ unsigned smem[32];
     __shared__ unsigned wsum[kTileThreads / 32];
     const int tile = blockIdx.x;
@@ -177,6 +180,7 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
 
 __global__ void alloc_finalize_kernel(const unsigned int* __restrict__ tile_sums, int n_tiles, Counters* ctr,
                                       long long cap) {
+    pdl_prologue();
     unsigned long long s = 0;
     for (int t = threadIdx.x; t < n_tiles; t += 32) s += tile_sums[t];
 #pragma unroll
@@ -199,6 +203,7 @@ __global__ void alloc_finalize_kernel(const unsigned int* __restrict__ tile_sums
 __global__ void __launch_bounds__(256) init_blocks_kernel(const Counters* __restrict__ ctr,
                                                           unsigned int* __restrict__ T, float2* __restrict__ P,
                                                           int t_words, unsigned int chi_word) {
+    pdl_prologue();
     const long long lo = ctr->n_blocks_prev, hi = ctr->n_blocks;
     for (long long b = lo + blockIdx.x; b < hi; b += gridDim.x) {
         for (int w = threadIdx.x; w < t_words; w += blockDim.x) T[b * t_words + w] = chi_word;
@@ -213,21 +218,21 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
     const long long n = (long long)p.width * p.height;
     if (n > 0) {
         const unsigned grid = (unsigned)((n + 255) / 256);
-        alloc_mark_kernel<<<grid, 256, 0, st>>>(depth, p, v->blk_slot, v->newbits);
+        launch_pdl(alloc_mark_kernel, dim3(grid), dim3(256), st, depth, p, v->blk_slot, v->newbits);
     }
-    alloc_count_kernel<<<v->n_tiles, kTileThreads, 0, st>>>(reinterpret_cast<const uint4*>(v->newbits),
-                                                            v->tile_sums);
-    alloc_assign_kernel<<<v->n_tiles, kTileThreads, 0, st>>>(v->newbits, v->tile_sums, v->ctr,
-                                                             v->blk_slot, v->blocks, v->cfg.block_capacity,
-                                                             frame, v->nb, v->occ2, v->occ3, v->n2, v->n3);
-    alloc_finalize_kernel<<<1, 32, 0, st>>>(v->tile_sums, (int)v->n_tiles, v->ctr, v->cfg.block_capacity);
+    launch_pdl(alloc_count_kernel, dim3(v->n_tiles), dim3(kTileThreads), st,
+               reinterpret_cast<const uint4*>(v->newbits), v->tile_sums);
+    launch_pdl(alloc_assign_kernel, dim3(v->n_tiles), dim3(kTileThreads), st, v->newbits, v->tile_sums, v->ctr,
+               v->blk_slot, v->blocks, v->cfg.block_capacity, frame, v->nb, v->occ2, v->occ3, v->n2, v->n3);
+    launch_pdl(alloc_finalize_kernel, dim3(1), dim3(32), st, v->tile_sums, (int)v->n_tiles, v->ctr,
+               v->cfg.block_capacity);
     const int bytes = storage_bytes(v->cfg.storage);
     const unsigned chi_word = v->cfg.storage == TSDF_STORAGE_F32   ? 0x7fc00000u
                               : v->cfg.storage == TSDF_STORAGE_F16 ? 0x7e007e00u
                                                                    : 0x80008000u;
-    init_blocks_kernel<<<v->num_sms * 4, 256, 0, st>>>(v->ctr, reinterpret_cast<unsigned int*>(v->T),
-                                                       reinterpret_cast<float2*>(v->P), kBlockVoxels * bytes / 4,
-                                                       chi_word);
+    launch_pdl(init_blocks_kernel, dim3(v->num_sms * 4), dim3(256), st, v->ctr,
+               reinterpret_cast<unsigned int*>(v->T), reinterpret_cast<float2*>(v->P), kBlockVoxels * bytes / 4,
+               chi_word);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ struct Candidate {
     int vpt, ctas, tw, th;
 };
 
-const int kCtaChoices[] = {4, 8, 12, 16, 24};
+const int kCtaChoices[] = {4, 8, 12, 16, 24, 32};
 const int kTiles[][2] = {{16, 8}, {8, 8}, {32, 4}, {8, 16}, {16, 16}};
 
 std::string cache_key(const tsdf_volume* v, const tsdf_intrinsics& K) {

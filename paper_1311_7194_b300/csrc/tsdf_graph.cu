@@ -7,7 +7,7 @@
 // place with the new kernel parameters (cudaGraphExecUpdate; the kernel
 // sequence never changes shape, so the update succeeds and no re-instantiation
 // is needed), and launches it on the caller's stream. The GPU then runs the
-// 14 (K = 1) or 5K + 10 small kernels back to back without per-kernel launch
+// 12 (K = 1) or 5K + 8 small kernels back to back without per-kernel launch
 // gaps. Optional caller events recorded at the stage boundaries become event
 // nodes of the graph, so stage times can still be measured per step.
 // Every size the kernels need lives in device counters, which is what

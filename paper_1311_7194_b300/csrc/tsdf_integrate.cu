@@ -78,10 +78,23 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
            vmin <= (float)p.height - 0.5f + pad;
 }
 
+// The integrate call's counters: the last call's counts go to the totals and
+// the per-call ones restart. Runs in the first kernel of the call, ahead of
+// every kernel that reads them (stream order).
+__device__ __forceinline__ void reset_frame_counters(Counters* ctr) {
+    ctr->updates_total += ctr->voxel_updates;
+    ctr->visible_total += ctr->n_visible;
+    ctr->n_visible = 0;
+    ctr->voxel_updates = 0;
+}
+
 // Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
-// the tile has none. One warp per tile, two pixels per lane.
+// the tile has none. One warp per tile, two pixels per lane. Thread 0 also
+// resets the call's counters when `reset` is given.
 __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth, FrameParams p,
-                                                          float2* __restrict__ tiles) {
+                                                          float2* __restrict__ tiles, Counters* __restrict__ reset) {
+    pdl_prologue();
+    if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
     const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
     const int lane = threadIdx.x & 31;
@@ -175,6 +188,7 @@ __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* _
 __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                    FrameParams p, const float2* __restrict__ tiles,
                                                    VisibleBlock* __restrict__ vis) {
+    pdl_prologue();
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -197,6 +211,7 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
 __global__ void __launch_bounds__(256) cull_batch_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                          BatchParams bp, const float2* __restrict__ tiles,
                                                          long long tiles_stride, VisibleBlock* __restrict__ vis) {
+    pdl_prologue();
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -360,12 +375,13 @@ __device__ __forceinline__ void update(const FrameParams& p, float& T, float& P,
 }
 
 template <bool kVarMap, int kS, int kVPT, int kRule, bool kRefine>
-__global__ void __launch_bounds__(kBlockVoxels / kVPT) integrate_kernel(Counters* __restrict__ ctr,
+__global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Counters* __restrict__ ctr,
                                                                         const VisibleBlock* __restrict__ vis,
                                                                         typename Codec<kS>::E* __restrict__ T,
                                                                         float* __restrict__ P,
                                                                         const float* __restrict__ depth,
                                                                         const float* __restrict__ var, FrameParams p) {
+    pdl_prologue();
     static_assert(kVPT == 4 || kVPT == 8, "a thread owns 4 or 8 consecutive voxels of an x row");
     const unsigned nvis = ctr->n_visible;
     const int v0 = threadIdx.x * kVPT;                    // first of this thread's voxels
@@ -424,6 +440,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
                                                                             const int4* __restrict__ blocks,
                                                                             typename Codec<kS>::E* __restrict__ T,
                                                                             float* __restrict__ P, BatchParams bp) {
+    pdl_prologue();
     const unsigned nvis = ctr->n_visible;
     const int v0 = threadIdx.x * 4;
     const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
@@ -476,12 +493,6 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
     if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
 }
 
-__global__ void reset_frame_counters(Counters* ctr) {
-    ctr->updates_total += ctr->voxel_updates;
-    ctr->visible_total += ctr->n_visible;
-    ctr->n_visible = 0;
-    ctr->voxel_updates = 0;
-}
 
 template <int kS, int kVPT, int kRule, bool kRefine>
 void launch_integrate_f(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
@@ -489,11 +500,11 @@ void launch_integrate_f(tsdf_volume* v, const float* depth, const float* var, co
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     constexpr int threads = kBlockVoxels / kVPT;
     if (var)
-        integrate_kernel<true, kS, kVPT, kRule, kRefine><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P, depth,
-                                                                                 var, p);
+        launch_pdl(integrate_kernel<true, kS, kVPT, kRule, kRefine>, dim3(grid), dim3(threads), st, v->ctr,
+                   v->visible, T, v->P, depth, var, p);
     else
-        integrate_kernel<false, kS, kVPT, kRule, kRefine><<<grid, threads, 0, st>>>(v->ctr, v->visible, T, v->P,
-                                                                                  depth, var, p);
+        launch_pdl(integrate_kernel<false, kS, kVPT, kRule, kRefine>, dim3(grid), dim3(threads), st, v->ctr,
+                   v->visible, T, v->P, depth, var, p);
 }
 
 // The refined measurement is instantiated for 4 voxels per thread only.
@@ -529,11 +540,11 @@ template <int kS, int kRule, bool kRefine>
 void launch_integrate_batch_f(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     if (bp.var[0])
-        integrate_batch_kernel<true, kS, kRule, kRefine><<<grid, kIntegrateThreads, 0, st>>>(
-            v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
+        launch_pdl(integrate_batch_kernel<true, kS, kRule, kRefine>, dim3(grid), dim3(kIntegrateThreads), st,
+                   v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
     else
-        integrate_batch_kernel<false, kS, kRule, kRefine><<<grid, kIntegrateThreads, 0, st>>>(
-            v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
+        launch_pdl(integrate_batch_kernel<false, kS, kRule, kRefine>, dim3(grid), dim3(kIntegrateThreads), st,
+                   v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
 }
 
 template <int kS, int kRule>
@@ -557,15 +568,14 @@ void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned gr
 
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
                              cudaStream_t st) {
-    reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
     if (!var && v->mlp_w) {
         // learned variance: the network's map feeds this frame's update
         const cudaError_t e = launch_variance_mlp(v, depth, p, v->var_map, st);
         if (e != cudaSuccess) return e;
         var = v->var_map;
     }
-    depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(depth, p, v->dtiles);
-    cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->dtiles, v->visible);
+    launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, depth, p, v->dtiles, v->ctr);
+    launch_pdl(cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, var, p, grid, st); break;
@@ -577,7 +587,6 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
 
 cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cudaStream_t st) {
     BatchParams bp = bp_in;
-    reset_frame_counters<<<1, 1, 0, st>>>(v->ctr);
     if (!bp.var[0] && v->mlp_w) {
         for (int k = 0; k < bp.K; ++k) {
             float* vk = v->var_batch + k * v->var_batch_stride;
@@ -587,10 +596,10 @@ cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cud
         }
     }
     for (int k = 0; k < bp.K; ++k)
-        depth_tiles_kernel<<<v->num_sms * 4, 256, 0, st>>>(bp.depth[k], bp.fp[k],
-                                                            v->dtiles_batch + k * v->dtiles_batch_stride);
-    cull_batch_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, bp, v->dtiles_batch,
-                                                      v->dtiles_batch_stride, v->visible_batch);
+        launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, bp.depth[k], bp.fp[k],
+                   v->dtiles_batch + k * v->dtiles_batch_stride, k == 0 ? v->ctr : nullptr);
+    launch_pdl(cull_batch_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, bp, v->dtiles_batch,
+               v->dtiles_batch_stride, v->visible_batch);
     const unsigned grid = (unsigned)v->num_sms * 12;
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_batch_s<TSDF_STORAGE_F16>(v, bp, grid, st); break;

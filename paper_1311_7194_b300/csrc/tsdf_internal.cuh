@@ -198,4 +198,33 @@ __device__ __forceinline__ unsigned int warp_sum(unsigned int x) {
     return __reduce_add_sync(0xffffffffu, x);
 }
 
+// Programmatic dependent launch. A kernel started by launch_pdl may be
+// scheduled while the kernel before it in the stream (or graph) is still
+// running; pdl_prologue(), the first statement of every such kernel, waits
+// until that kernel has completed and its writes are visible (so nothing is
+// read early), then allows the kernel after this one to be scheduled in turn.
+// The launch latency of each kernel thus overlaps its predecessor's tail, one
+// kernel ahead. Both instructions do nothing when the kernel was launched
+// without the attribute.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a failed launch leaves its error for the caller's cudaGetLastError()
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace tsdf

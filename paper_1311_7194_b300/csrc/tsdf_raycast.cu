@@ -74,6 +74,7 @@ __device__ __forceinline__ void block_box(const FrameParams& p, int4 bc, float z
 
 __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                       FrameParams p, int* __restrict__ vis) {
+    pdl_prologue();
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -98,7 +99,20 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
     }
 }
 
-__global__ void range_clear_kernel(unsigned int* __restrict__ near_, unsigned int* __restrict__ far_, long long n) {
+// The raycast call's counters: the last call's counts go to the totals and the
+// per-call ones restart (thread 0 of the call's first kernel).
+__device__ __forceinline__ void reset_rc_counters(Counters* ctr) {
+    ctr->rc_next = 0;
+    ctr->rays_total += ctr->rays_hit;
+    ctr->rc_blocks_total += ctr->n_visible_rc;
+    ctr->n_visible_rc = 0;
+    ctr->rays_hit = 0;
+}
+
+__global__ void range_clear_kernel(unsigned int* __restrict__ near_, unsigned int* __restrict__ far_, long long n,
+                                   Counters* __restrict__ ctr) {
+    pdl_prologue();
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_rc_counters(ctr);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         near_[i] = kNearInit;
         far_[i] = kFarInit;
@@ -108,6 +122,7 @@ __global__ void range_clear_kernel(unsigned int* __restrict__ near_, unsigned in
 __global__ void __launch_bounds__(256) raster_kernel(const Counters* __restrict__ ctr, const int* __restrict__ vis,
                                                      const int4* __restrict__ blocks, FrameParams p,
                                                      unsigned int* __restrict__ near_, unsigned int* __restrict__ far_) {
+    pdl_prologue();
     const unsigned n = ctr->n_visible_rc;
     const int lane = threadIdx.x & 31;
     const int tiles_x = (p.width + kRangeTile - 1) / kRangeTile;
@@ -311,6 +326,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                                                       const unsigned int* __restrict__ occ3,
                                                       float* __restrict__ depth_out, float* __restrict__ normal_out,
                                                       float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
+    pdl_prologue();
     const int u = blockIdx.x * kTW + (threadIdx.x % kTW);
     const int v = blockIdx.y * kTH + (threadIdx.x / kTW);
     const bool in = u < p.width && v < p.height;
@@ -550,6 +566,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
     const unsigned int* __restrict__ occ3, float* __restrict__ depth_out, float* __restrict__ normal_out,
     float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
+    pdl_prologue();
     // bracket queue of each warp: pix, z1, f1, z2, f2, dq (x, y, z)
     __shared__ float sq[kRcWarps][8][kQueue];
     float(*q)[kQueue] = sq[threadIdx.x >> 5];
@@ -730,22 +747,14 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     if (lane == 0 && hits) atomicAdd(&ctr->rays_hit, (unsigned long long)hits);
 }
 
-__global__ void reset_rc_counters(Counters* ctr) {
-    ctr->rc_next = 0;
-    ctr->rays_total += ctr->rays_hit;
-    ctr->rc_blocks_total += ctr->n_visible_rc;
-    ctr->n_visible_rc = 0;
-    ctr->rays_hit = 0;
-}
 
 template <int kS, int kTW, int kTH>
 void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const dim3 grid((unsigned)((p.width + kTW - 1) / kTW), (unsigned)((p.height + kTH - 1) / kTH));
-    raycast_kernel<kS, kTW, kTH><<<grid, kTW * kTH, 0, st>>>(p, near_, far_, v->blk_slot,
-                                                             static_cast<const typename Codec<kS>::E*>(v->T),
-                                                             v->occ2, v->occ3, depth_out, normal_out, vertex_out,
-                                                             v->ctr);
+    launch_pdl(raycast_kernel<kS, kTW, kTH>, grid, dim3(kTW * kTH), st, p, near_, far_, v->blk_slot,
+               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out, normal_out, vertex_out,
+               v->ctr);
 }
 
 // Raycast tile shapes the autotuner chooses from (pixels per CTA, width x height).
@@ -759,9 +768,9 @@ void launch_persistent(tsdf_volume* v, const FrameParams& p, const unsigned int*
                                                        0) != cudaSuccess ||
          per_sm < 1))
         per_sm = 1;
-    raycast_persistent_kernel<kS, kNarrow><<<v->num_sms * per_sm, 32 * kRcWarps, 0, st>>>(
-        p, near_, far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
-        normal_out, vertex_out, v->ctr);
+    launch_pdl(raycast_persistent_kernel<kS, kNarrow>, dim3(v->num_sms * per_sm), dim3(32 * kRcWarps), st, p, near_,
+               far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
+               normal_out, vertex_out, v->ctr);
 }
 
 template <int kS>
@@ -811,10 +820,9 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
                            ((p.height + kRangeTile - 1) / kRangeTile);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_pixels;
-    reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
-    range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
-    rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
-    raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
+    launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
+    launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
@@ -834,9 +842,8 @@ template <int kS>
 void launch_march_traced(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                          cudaStream_t st) {
     const dim3 grid((p.width + 15) / 16, (p.height + 7) / 8);
-    raycast_kernel<kS, 16, 8, true><<<grid, 128, 0, st>>>(p, near_, far_, v->blk_slot,
-                                                         static_cast<const typename Codec<kS>::E*>(v->T), v->occ2,
-                                                         v->occ3, nullptr, nullptr, nullptr, v->ctr);
+    launch_pdl(raycast_kernel<kS, 16, 8, true>, grid, dim3(128), st, p, near_, far_, v->blk_slot,
+               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, nullptr, nullptr, nullptr, v->ctr);
 }
 
 }  // namespace
@@ -851,10 +858,9 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
                            ((p.height + kRangeTile - 1) / kRangeTile);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_pixels;
-    reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
-    range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
-    rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
-    raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
+    launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
+    launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_march_traced<TSDF_STORAGE_F16>(v, p, near_, far_, st); break;
         case TSDF_STORAGE_SNORM16: launch_march_traced<TSDF_STORAGE_SNORM16>(v, p, near_, far_, st); break;
@@ -869,10 +875,9 @@ cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
                            ((p.height + kRangeTile - 1) / kRangeTile);
-    reset_rc_counters<<<1, 1, 0, st>>>(v->ctr);
-    range_clear_kernel<<<v->num_sms * 4, 256, 0, st>>>(near_, far_, npix);
-    rc_cull_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->blocks, p, v->visible_rc);
-    raster_kernel<<<v->num_sms * 8, 256, 0, st>>>(v->ctr, v->visible_rc, v->blocks, p, near_, far_);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
+    launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
+    launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
