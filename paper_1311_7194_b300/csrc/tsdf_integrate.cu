@@ -23,9 +23,11 @@
 // z_lo + dz is small, and the result keeps full precision. x and y only choose
 // the pixel and need no such care.
 //
-// A voxel whose camera z lies outside the block's reach of the band (the depth
-// range under the block's footprint widened by delta, from the cull) is
-// rejected before any projection: it cannot have |T_k| <= delta.
+// In the batched kernel a voxel whose camera z lies outside the block's reach of
+// the band (the depth range under the block's footprint widened by delta, from
+// the cull) is rejected before any projection: it cannot have |T_k| <= delta.
+// That range is what marks the frames of a batch a block cannot reach; for a
+// single frame it rejects few voxels, and the projection goes first.
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -314,20 +316,27 @@ __device__ __forceinline__ float refine_tk(const FrameParams& p, const float* __
     return dist < 0.0f ? t0 : side * dist;
 }
 
-template <bool kVarMap, bool kRefine>
+// kZRange: reject voxels outside the entry's camera-z range [zlo, zhi] first.
+// The batched kernel needs it (an entry of a frame the block cannot reach
+// carries an empty range); in the single-frame kernel the range from the
+// depth tiles rejects few voxels, and the band test alone decides.
+template <bool kVarMap, bool kRefine, bool kZRange = true>
 __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
                                         float zr, const float* __restrict__ depth, const float* __restrict__ var,
                                         float* Tk, float* pk) {
     const float zs = __fmaf_rn(lx, p.cs[6], zr);
     const float z = __fadd_rn(vb.o[2], zs);
-    if (!(z > 0.0f && z >= vb.zlo && z <= vb.zhi)) return false;   // out of reach of the band
+    if (kZRange ? !(z > 1e-30f && z >= vb.zlo && z <= vb.zhi) : !(z > 1e-30f)) return false;
     const float x = __fmaf_rn(lx, p.cs[0], xr);
     const float y = __fmaf_rn(lx, p.cs[3], yr);
     const float rz = rcp_newton(z);
     const float uf = __fmaf_rn(p.fx, __fmul_rn(x, rz), p.cxh);   // u + 1/2
     const float vf = __fmaf_rn(p.fy, __fmul_rn(y, rz), p.cyh);
-    if (!(uf >= 0.0f && uf < (float)p.width && vf >= 0.0f && vf < (float)p.height)) return false;
-    const int pix = (int)floorf(vf) * p.width + (int)floorf(uf);
+    // nearest pixel: floor(u + 1/2) in [0, W) (z > 1e-30 keeps u, v finite; a
+    // value beyond the int range saturates and fails the unsigned test)
+    const int ui = __float2int_rd(uf), vi = __float2int_rd(vf);
+    if ((unsigned)ui >= (unsigned)p.width || (unsigned)vi >= (unsigned)p.height) return false;
+    const int pix = vi * p.width + ui;
     const float D = __ldg(depth + pix);
     // the band test first: most voxels that get here fail it
     const float t = __fsub_rn(__fsub_rn(D, vb.o[2]), zs);
@@ -398,7 +407,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
         bool any = false;
 #pragma unroll
         for (int e = 0; e < kVPT; ++e) {
-            ok[e] = measure<kVarMap, kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
+            ok[e] = measure<kVarMap, kRefine, false>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
             any |= ok[e];
         }
         if (!any) continue;
