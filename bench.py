@@ -229,13 +229,13 @@ def _sha(path):
 # with the hash of the kernel source it was measured on; a value is dropped
 # when that source changes.
 NCU_TRAFFIC = {
-    # frames 100-109, 10 launches each of depth_tiles + cull + integrate + reset:
-    # 2098.2 MB over 76.55 M voxel updates
-    "integrate": {"sha": "05265be1a6d77b34", "bytes_per_unit": 27.41},
-    # same frames, 10 launches each of reset + clear + range cull + raster +
-    # persistent raycast: 1015.2 MB against 816.0 MB of traced unique bytes,
+    # frames 100-109, 10 launches each of depth_tiles + cull + integrate:
+    # 2096.9 MB over 76.55 M voxel updates
+    "integrate": {"sha": "aef8d58e3d54a5a1", "bytes_per_unit": 27.39},
+    # same frames, 10 launches each of clear + range cull + raster +
+    # persistent raycast: 1015.6 MB against 816.0 MB of traced unique bytes,
     # i.e. DRAM bytes per algorithmic byte
-    "raycast": {"sha": "d5f52604ae415e3a", "bytes_per_unit": 1.2441},
+    "raycast": {"sha": "c3c79ba82ca7facb", "bytes_per_unit": 1.2446},
 }
 STAGE_SOURCES = {"integrate": "tsdf_integrate.cu", "raycast": "tsdf_raycast.cu"}
 TRACE_EVERY = 10
