@@ -6,8 +6,9 @@
 //   1. alloc_mark:   one thread per pixel samples its ray at 2J+1 depths in
 //                    [D - delta, D + delta]; every sample's block that the block
 //                    table marks empty gets its bit set in a new-block bitmap
-//                    (consecutive samples of a pixel and lanes of a warp that hit
-//                    the same block are merged first, so few atomics remain).
+//                    (consecutive samples of a pixel in the same block are
+//                    merged, and a bit already set is not set again, so few
+//                    atomics remain).
 //   2. alloc_count:  per 4096-word tile of the bitmap, the number of new blocks.
 //   3. alloc_assign: each tile ranks its new blocks after all earlier tiles', so
 //                    slots follow ascending block key whatever the order in
@@ -29,7 +30,6 @@ __global__ void __launch_bounds__(256) alloc_mark_kernel(const float* __restrict
                                                          const int* __restrict__ blk_slot,
                                                          unsigned int* __restrict__ newbits) {
     pdl_prologue();
-    const int lane = threadIdx.x & 31;
     const long long n = (long long)p.width * p.height;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float d = 0.0f;
@@ -46,7 +46,6 @@ __global__ void __launch_bounds__(256) alloc_mark_kernel(const float* __restrict
         b2 = __fmaf_rn(p.M[6], xn, __fmaf_rn(p.M[7], yn, p.M[8]));
     }
     unsigned last = kNoKey;
-    // Every lane runs the same 2J+1 iterations so that warp votes stay converged.
     for (int k = 0; k <= 2 * p.J; ++k) {
         unsigned key = kNoKey;
         if (valid) {
@@ -63,14 +62,10 @@ __global__ void __launch_bounds__(256) alloc_mark_kernel(const float* __restrict
         }
         const bool fresh = key != kNoKey && key != last;
         if (key != kNoKey) last = key;
-        const unsigned want = __ballot_sync(0xffffffffu, fresh);
-        if (fresh) {
-            const unsigned peers = __match_any_sync(want, key);
-            if (lane == __ffs(peers) - 1 && __ldg(blk_slot + key) < 0) {
-                const unsigned bit = 1u << (key & 31u);
-                unsigned int* w = newbits + (key >> 5);
-                if (!(*(volatile unsigned int*)w & bit)) atomicOr(w, bit);
-            }
+        if (fresh && __ldg(blk_slot + key) < 0) {
+            const unsigned bit = 1u << (key & 31u);
+            unsigned int* w = newbits + (key >> 5);
+            if (!(*(volatile unsigned int*)w & bit)) atomicOr(w, bit);
         }
     }
 }
