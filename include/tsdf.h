@@ -485,6 +485,51 @@ tsdf_status tsdf_get_status(tsdf_volume* vol);
 /* Synchronise and copy the counters into *out (host). */
 tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
 
+/* The volume's configuration as it is now (tsdf_shift moves the origin).
+ * Errors: TSDF_ERR_INVALID_ARG. */
+tsdf_status tsdf_get_config(const tsdf_volume* vol, tsdf_config* out);
+
+/* Block eviction (section "Discussion": the TSDF data of occupied blocks goes
+ * to host storage so that scenes larger than device memory can be scanned).
+ * Every allocated block whose block coordinates lie outside the box
+ * [lo, hi) (per axis, block units) is removed from the volume and copied to
+ * HOST buffers in pool order: coords_frame n x 4 int32 (bx, by, bz,
+ * allocation frame), T n x 512 float32 decoded from the storage format
+ * (chi = NaN), P n x 512 float32; any of the three may be NULL. *n_evicted
+ * receives n. The kept blocks keep their data bit for bit; the pool is
+ * compacted (the last kept blocks move into the freed slots) and the block
+ * table and occupancy maps are updated. Synchronous; allocates and frees a
+ * staging buffer of n x 4 KB on the device.
+ * Errors: TSDF_ERR_INVALID_ARG (NULL vol / lo / hi / n_evicted, lo > hi on an
+ * axis, max_blocks < 0); TSDF_ERR_CAPACITY when n > max_blocks, with
+ * *n_evicted = n and nothing changed; TSDF_ERR_CUDA. */
+tsdf_status tsdf_evict(tsdf_volume* vol, const int32_t lo[3], const int32_t hi[3], int64_t max_blocks,
+                       int32_t* coords_frame, float* T, float* P, int64_t* n_evicted, void* stream);
+
+/* Volume shift (section "Discussion": the shift evicts the TSDF data of the
+ * blocks that leave the volume and rebuilds the offset array). The grid moves
+ * by d whole blocks: origin += 8 * voxel_size * d, so a voxel keeps its world
+ * position and its block coordinates become b - d. Blocks whose new
+ * coordinates fall outside [0, grid_dim / 8) are evicted first, exactly as
+ * tsdf_evict does (same outputs, coordinates before the shift); the block
+ * table is then rebuilt from the kept blocks. The new origin is read back with
+ * tsdf_get_config. Errors: those of tsdf_evict (nothing changes on an error),
+ * TSDF_ERR_INVALID_ARG for |d| >= 2^24 on an axis. */
+tsdf_status tsdf_shift(tsdf_volume* vol, const int32_t d[3], int64_t max_blocks, int32_t* coords_frame,
+                       float* T, float* P, int64_t* n_evicted, void* stream);
+
+/* Bring evicted blocks back: n blocks from HOST buffers laid out as
+ * tsdf_evict writes them (the allocation-frame column is ignored: an imported
+ * block counts as allocated at the current frame). T is encoded to the
+ * storage format (a block evicted from a volume of the same format comes back
+ * bit for bit). Synchronous.
+ * Errors: TSDF_ERR_INVALID_ARG (NULL buffers with n > 0, n < 0, coordinates
+ * outside the grid, a block given twice or already allocated - nothing is
+ * changed then); TSDF_ERR_CAPACITY when the pool cannot hold n more blocks;
+ * TSDF_ERR_CUDA. */
+tsdf_status tsdf_import(tsdf_volume* vol, int64_t n, const int32_t* coords_frame, const float* T, const float* P,
+                        void* stream);
+
 /* Copy the volume to HOST buffers in pool order (synchronises). For n blocks:
  * coords_frame: n x 4 int32 (bx, by, bz, allocation frame); T: n x 512 float32
  * decoded from the storage format (chi = NaN); P: n x 512 float32 (unspecified

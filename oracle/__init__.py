@@ -99,6 +99,11 @@ def _load(path: Optional[str] = None) -> ctypes.CDLL:
         "ov_mlp_forward": (None, [_D, ctypes.c_int64, _D, _D]),
         "ov_mlp_loss_grad": (None, [_D, ctypes.c_int64, _D, _D, _D, _D]),
         "ov_mlp_variance_map": (None, [_D, _F, ctypes.POINTER(_Intr), ctypes.POINTER(_Params), _F]),
+        "ov_count_outside": (ctypes.c_int64, [_P, _I32, _I32]),
+        "ov_evict": (ctypes.c_int64, [_P, _I32, _I32, _I32, _D, _D]),
+        "ov_shift": (ctypes.c_int64, [_P, _I32, _I32, _D, _D]),
+        "ov_import": (ctypes.c_int32, [_P, ctypes.c_int64, _I32, _D, _D, ctypes.c_int32]),
+        "ov_origin": (None, [_P, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +250,51 @@ class OracleVolume:
                             _ptr(vert, _D), _ptr(nrm, _D), _ptr(flags, _I32))
         return depth, vert, nrm, flags
 
+
+    # Eviction and volume shift (section "Discussion"): see ov_evict / ov_shift.
+    def _take(self, n, call) -> Export:
+        cf = np.empty((n, 4), np.int32)
+        T = np.empty((n, 512)); P = np.empty((n, 512))
+        m = call(_ptr(cf, _I32), _ptr(T, _D), _ptr(P, _D))
+        assert m == n
+        return Export(cf[:, :3].copy(), cf[:, 3].copy(), T, P, np.zeros((n, 512), bool))
+
+    def evict(self, lo, hi) -> Export:
+        """Remove and return (ascending key order) every block outside the box [lo, hi)."""
+        a = np.ascontiguousarray(lo, np.int32); b = np.ascontiguousarray(hi, np.int32)
+        n = int(self.lib.ov_count_outside(self.h, _ptr(a, _I32), _ptr(b, _I32)))
+        return self._take(n, lambda cf, T, P: self.lib.ov_evict(self.h, _ptr(a, _I32), _ptr(b, _I32), cf, T, P))
+
+    def shift(self, d) -> Export:
+        """Move the grid by d blocks; return the blocks that left it."""
+        dd = np.ascontiguousarray(d, np.int32)
+        nb = int(self.params.grid_dim) // 8
+        lo = dd.copy(); hi = dd + nb
+        n = int(self.lib.ov_count_outside(self.h, _ptr(lo, _I32), _ptr(hi, _I32)))
+        out = self._take(n, lambda cf, T, P: self.lib.ov_shift(self.h, _ptr(dd, _I32), cf, T, P))
+        o = np.empty(3)
+        self.lib.ov_origin(self.h, _ptr(o, _D))
+        self.params.origin = (ctypes.c_double * 3)(*o)
+        return out
+
+    @property
+    def origin(self) -> np.ndarray:
+        o = np.empty(3)
+        self.lib.ov_origin(self.h, _ptr(o, _D))
+        return o
+
+    def import_blocks(self, coords, T, P, frame: Optional[int] = None):
+        """Add blocks (coords (n, 3), T and P (n, 512), NaN T = chi) at the
+        current frame; raises ValueError when the oracle refuses them."""
+        coords = np.asarray(coords, np.int32)
+        n = coords.shape[0]
+        cf = np.zeros((n, 4), np.int32)
+        cf[:, :3] = coords[:, :3]
+        T = np.ascontiguousarray(T, np.float64).reshape(n, 512)
+        P = np.ascontiguousarray(P, np.float64).reshape(n, 512)
+        fr = self.frame if frame is None else frame
+        if self.lib.ov_import(self.h, n, _ptr(cf, _I32), _ptr(T, _D), _ptr(P, _D), fr) != 0:
+            raise ValueError("oracle: import refused")
 
     def field(self, points: np.ndarray) -> np.ndarray:
         """Trilinear field at world points (n, 3); NaN where undefined."""

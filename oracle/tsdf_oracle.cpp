@@ -670,6 +670,61 @@ RayOut cast_ray(const Volume& v, const ov_intr& in, const double* pose, int32_t 
     return out;
 }
 
+// --------------------------------------------------------------------------
+// Eviction and volume shift (section "Discussion")
+// --------------------------------------------------------------------------
+// The paper names both for scenes beyond device memory: the TSDF data of the
+// occupied blocks is evicted to other storage, and a shift of the volume evicts
+// the blocks that leave it and rebuilds the offset array. Readings:
+//   * eviction removes every block whose block coordinates lie outside a box
+//     [lo, hi) and hands out its coordinates, allocation frame and values;
+//   * a shift by d moves the grid by whole blocks: origin' = origin + 8 s d, so
+//     voxel i' = i - 8 d sits where voxel i sat; blocks whose new coordinates
+//     b - d leave [0, nb) are evicted first;
+//   * an imported block is allocated at the given frame with the given values.
+
+bool outside_box(const Block& b, const int32_t lo[3], const int32_t hi[3]) {
+    for (int r = 0; r < 3; ++r)
+        if (b.b[r] < lo[r] || b.b[r] >= hi[r]) return true;
+    return false;
+}
+
+void rebuild_index(Volume& v) {
+    v.index.clear();
+    for (size_t i = 0; i < v.blocks.size(); ++i)
+        v.index.emplace(block_key(v.blocks[i].b[0], v.blocks[i].b[1], v.blocks[i].b[2], v.nb), (int32_t)i);
+}
+
+// Removes the blocks outside [lo, hi); writes them in ascending key order.
+int64_t evict_box(Volume& v, const int32_t lo[3], const int32_t hi[3], int32_t* coords_frame, double* T,
+                  double* P) {
+    std::vector<std::pair<uint32_t, size_t>> gone;
+    for (size_t i = 0; i < v.blocks.size(); ++i)
+        if (outside_box(v.blocks[i], lo, hi))
+            gone.emplace_back(block_key(v.blocks[i].b[0], v.blocks[i].b[1], v.blocks[i].b[2], v.nb), i);
+    std::sort(gone.begin(), gone.end());
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (size_t n = 0; n < gone.size(); ++n) {
+        const Block& b = v.blocks[gone[n].second];
+        if (coords_frame) {
+            for (int r = 0; r < 3; ++r) coords_frame[4 * n + r] = b.b[r];
+            coords_frame[4 * n + 3] = b.alloc_frame;
+        }
+        if (!v.p.store_values) continue;
+        for (int l = 0; l < M3; ++l) {
+            if (T) T[n * M3 + l] = b.chi[l] ? nan : b.T[l];
+            if (P) P[n * M3 + l] = b.chi[l] ? nan : b.P[l];
+        }
+    }
+    std::vector<Block> kept;
+    kept.reserve(v.blocks.size() - gone.size());
+    for (Block& b : v.blocks)
+        if (!outside_box(b, lo, hi)) kept.push_back(std::move(b));
+    v.blocks = std::move(kept);
+    rebuild_index(v);
+    return (int64_t)gone.size();
+}
+
 }  // namespace
 
 // ==========================================================================
@@ -754,6 +809,83 @@ void ov_export(const void* h, int32_t* coords_frame, double* T, double* P, uint8
             if (amb) amb[n * M3 + l] = b.amb[l];
         }
     }
+}
+
+// Number of blocks outside the block box [lo, hi).
+int64_t ov_count_outside(const void* h, const int32_t* lo, const int32_t* hi) {
+    const Volume& v = *static_cast<const Volume*>(h);
+    int64_t n = 0;
+    for (const Block& b : v.blocks) n += outside_box(b, lo, hi);
+    return n;
+}
+
+// Evicts the blocks outside [lo, hi) into the buffers (ascending key order,
+// layout of ov_export); returns their number.
+int64_t ov_evict(void* h, const int32_t* lo, const int32_t* hi, int32_t* coords_frame, double* T, double* P) {
+    return evict_box(*static_cast<Volume*>(h), lo, hi, coords_frame, T, P);
+}
+
+// Shifts the grid by d blocks; the blocks that leave it are written as by
+// ov_evict (coordinates before the shift).
+int64_t ov_shift(void* h, const int32_t* d, int32_t* coords_frame, double* T, double* P) {
+    Volume& v = *static_cast<Volume*>(h);
+    int32_t lo[3], hi[3];
+    for (int r = 0; r < 3; ++r) {
+        lo[r] = d[r];
+        hi[r] = d[r] + v.nb;
+    }
+    const int64_t n = evict_box(v, lo, hi, coords_frame, T, P);
+    for (Block& b : v.blocks)
+        for (int r = 0; r < 3; ++r) b.b[r] -= d[r];
+    rebuild_index(v);
+    for (int r = 0; r < 3; ++r) v.p.origin[r] += (double)((int64_t)M * d[r]) * (double)v.p.voxel_size;
+    return n;
+}
+
+// Adds n blocks with the given values (NaN T = chi) at allocation frame
+// `frame`. Returns 0, or -1 (nothing added) when a block lies outside the grid,
+// is given twice or is already allocated, or the pool would overflow.
+int32_t ov_import(void* h, int64_t n, const int32_t* coords_frame, const double* T, const double* P, int32_t frame) {
+    Volume& v = *static_cast<Volume*>(h);
+    std::vector<uint32_t> keys;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t* c = coords_frame + 4 * i;
+        for (int r = 0; r < 3; ++r)
+            if (c[r] < 0 || c[r] >= v.nb) return -1;
+        keys.push_back(block_key(c[0], c[1], c[2], v.nb));
+        if (v.index.count(keys.back())) return -1;
+    }
+    std::vector<uint32_t> sorted(keys);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return -1;
+    if ((int64_t)v.blocks.size() + n > v.p.block_capacity) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        Block blk;
+        for (int r = 0; r < 3; ++r) blk.b[r] = coords_frame[4 * i + r];
+        blk.alloc_frame = frame;
+        if (v.p.store_values) {
+            blk.T.assign(M3, 0.0);
+            blk.P.assign(M3, 0.0);
+            blk.chi.assign(M3, 1);
+            blk.amb.assign(M3, 0);
+            for (int l = 0; l < M3; ++l) {
+                const double t = T[i * M3 + l];
+                if (std::isnan(t)) continue;
+                blk.chi[l] = 0;
+                blk.T[l] = t;
+                blk.P[l] = P[i * M3 + l];
+            }
+        }
+        v.index.emplace(keys[i], (int32_t)v.blocks.size());
+        v.blocks.push_back(std::move(blk));
+    }
+    return 0;
+}
+
+// The volume's origin (it moves with ov_shift).
+void ov_origin(const void* h, double* out) {
+    const Volume& v = *static_cast<const Volume*>(h);
+    for (int r = 0; r < 3; ++r) out[r] = v.p.origin[r];
 }
 
 void ov_raycast(const void* h, const ov_intr* in, const double* pose, int64_t n,

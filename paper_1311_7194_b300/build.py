@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsdf.so")
 SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu", "tsdf_graph.cu",
-           "tsdf_autotune.cu", "tsdf_mlp.cu", "tsdf_icp.cu", "tsdf_mesh.cu"]
+           "tsdf_autotune.cu", "tsdf_mlp.cu", "tsdf_icp.cu", "tsdf_mesh.cu", "tsdf_evict.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # No FMA contraction: every fused multiply-add is written out (__fmaf_rn), so the
 # allocation arithmetic and the Kalman update are the same op sequence wherever

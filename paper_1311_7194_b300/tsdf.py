@@ -29,7 +29,8 @@ EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_cr
             "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
             "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
             "tsdf_quadratic_variance",
-            "tsdf_get_status", "tsdf_get_stats", "tsdf_export"]
+            "tsdf_get_status", "tsdf_get_stats", "tsdf_export", "tsdf_get_config", "tsdf_evict", "tsdf_shift",
+            "tsdf_import"]
 
 
 class TsdfError(RuntimeError):
@@ -163,6 +164,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_get_status": (ctypes.c_int, [_P]),
         "tsdf_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
         "tsdf_export": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+        "tsdf_get_config": (ctypes.c_int, [_P, ctypes.POINTER(Config)]),
+        "tsdf_evict": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.c_int64, _P, _P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+        "tsdf_shift": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, _P, _P, _P,
+                                      ctypes.POINTER(ctypes.c_int64), _P]),
+        "tsdf_import": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,6 +285,17 @@ class Export:
         key = self.coords[:, 0].astype(np.int64) + nb * (self.coords[:, 1] + nb * self.coords[:, 2].astype(np.int64))
         o = np.argsort(key, kind="stable")
         return Export(self.coords[o], self.alloc_frame[o], self.T[o], self.P[o])
+
+
+@dataclass
+class Evicted:
+    """Blocks removed by Volume.evict / Volume.shift, in pool order: block
+    coordinates (n, 3) before the call, allocation frames (n,), T (n, 512)
+    float32 (NaN = chi) and P (n, 512)."""
+    coords: np.ndarray
+    frames: np.ndarray
+    T: np.ndarray
+    P: np.ndarray
 
 
 class Volume:
@@ -481,6 +499,59 @@ class Volume:
         _check(self.lib.tsdf_export(self.h, cf.ctypes.data_as(_P), T.ctypes.data_as(_P) if values else None,
                                     P.ctypes.data_as(_P) if values else None, m, ctypes.byref(n)), "tsdf_export")
         return Export(cf[:, :3].copy(), cf[:, 3].copy(), T, P)
+
+    def get_config(self) -> Config:
+        """tsdf_get_config: the volume's configuration now (the origin moves with shift)."""
+        c = Config()
+        _check(self.lib.tsdf_get_config(self.h, ctypes.byref(c)), "tsdf_get_config")
+        return c
+
+    @property
+    def origin(self) -> tuple:
+        return tuple(float(x) for x in self.get_config().origin)
+
+    def _evicted(self, call, what: str) -> Evicted:
+        n = ctypes.c_int64(0)
+        st = call(0, None, None, None, ctypes.byref(n))
+        if st == OK:
+            m = 0
+        elif st == ERR_CAPACITY:
+            m = int(n.value)
+        else:
+            _check(st, what)
+        cf = np.empty((m, 4), np.int32)
+        T = np.empty((m, 512), np.float32)
+        P = np.empty((m, 512), np.float32)
+        if m:
+            _check(call(m, cf.ctypes.data_as(_P), T.ctypes.data_as(_P), P.ctypes.data_as(_P), ctypes.byref(n)), what)
+        return Evicted(cf[:, :3].copy(), cf[:, 3].copy(), T, P)
+
+    def evict(self, lo, hi, stream=None) -> Evicted:
+        """tsdf_evict: remove and return every block outside the block box [lo, hi)."""
+        a = (ctypes.c_int32 * 3)(*[int(x) for x in lo])
+        b = (ctypes.c_int32 * 3)(*[int(x) for x in hi])
+        return self._evicted(lambda m, cf, T, P, n: self.lib.tsdf_evict(self.h, a, b, m, cf, T, P, n,
+                                                                         _stream(stream)), "tsdf_evict")
+
+    def shift(self, d, stream=None) -> Evicted:
+        """tsdf_shift: move the grid by d blocks (origin += 8 s d); returns the
+        blocks that left it."""
+        dd = (ctypes.c_int32 * 3)(*[int(x) for x in d])
+        out = self._evicted(lambda m, cf, T, P, n: self.lib.tsdf_shift(self.h, dd, m, cf, T, P, n, _stream(stream)),
+                            "tsdf_shift")
+        self.config = self.get_config()
+        return out
+
+    def import_blocks(self, coords, T, P, stream=None):
+        """tsdf_import: add blocks (coords (n, 3) or (n, 4), T and P (n, 512))."""
+        coords = np.asarray(coords, np.int32)
+        n = coords.shape[0]
+        cf = np.zeros((n, 4), np.int32)
+        cf[:, :3] = coords[:, :3]
+        T = np.ascontiguousarray(T, np.float32).reshape(n, 512)
+        P = np.ascontiguousarray(P, np.float32).reshape(n, 512)
+        _check(self.lib.tsdf_import(self.h, n, cf.ctypes.data_as(_P), T.ctypes.data_as(_P), P.ctypes.data_as(_P),
+                                    _stream(stream)), "tsdf_import")
 
 
 class Graph:

@@ -814,13 +814,150 @@ def pin_mesh_every_case_closed(lib_path=None):
         assert sorted(e for l in omesh.case_polygons(ins) for e in l) == crossed, case
 
 
+# ----------------------------------------------------------------------------
+# eviction and volume shift (section "Discussion")
+# ----------------------------------------------------------------------------
+
+def _fused(seq, n, lib_path=None):
+    ov = oracle.OracleVolume(seq.volume, seq.intr, lib_path=lib_path, amb_px=5e-4)
+    for k in range(n):
+        ov.fuse(seq.depth[k], seq.poses[k])
+    return ov
+
+
+def _by_key(e, nb):
+    key = e.coords[:, 0].astype(np.int64) + nb * (e.coords[:, 1] + nb * e.coords[:, 2].astype(np.int64))
+    o = np.argsort(key)
+    return key[o], e.T[o], e.P[o], e.alloc_frame[o]
+
+
+def _same_values(a, b):
+    return np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(np.nan_to_num(a), np.nan_to_num(b))
+
+
+def pin_evict_takes_the_blocks_outside_the_box_and_import_restores(lib_path=None):
+    """Eviction is bookkeeping: the evicted blocks are exactly those a brute-force
+    test of the exported coordinates puts outside the box, with their exported
+    values; the kept ones are untouched; importing the evicted ones restores
+    the volume (section "Discussion")."""
+    sphere = synth.sphere_sequence(n_frames=4)
+    ov = _fused(sphere, 4, lib_path)
+    nb = sphere.volume.grid_dim // 8
+    before = ov.export()
+    lo, hi = np.array([5, 10, 8]), np.array([20, 30, 16])
+    out = np.any((before.coords < lo) | (before.coords >= hi), axis=1)
+    assert 0 < out.sum() < len(out)
+    ev = ov.evict(lo, hi)
+    # the evicted set, by brute force over the exported coordinates
+    k_ev, T_ev, P_ev, f_ev = _by_key(ev, nb)
+    sel = oracle.Export(before.coords[out], before.alloc_frame[out], before.T[out], before.P[out], before.amb[out])
+    k_ref, T_ref, P_ref, f_ref = _by_key(sel, nb)
+    assert np.array_equal(k_ev, k_ref) and np.array_equal(f_ev, f_ref)
+    assert _same_values(T_ev, T_ref) and _same_values(P_ev, P_ref)
+    # the kept ones, untouched
+    after = ov.export()
+    assert len(after.coords) == int((~out).sum())
+    assert not np.any((after.coords < lo) | (after.coords >= hi))
+    keep = oracle.Export(before.coords[~out], before.alloc_frame[~out], before.T[~out], before.P[~out],
+                         before.amb[~out])
+    ka, Ta, Pa, _ = _by_key(after, nb)
+    kk, Tk, Pk, _ = _by_key(keep, nb)
+    assert np.array_equal(ka, kk) and _same_values(Ta, Tk) and _same_values(Pa, Pk)
+    # and back: the whole volume again (imported blocks count as allocated now)
+    ov.import_blocks(ev.coords, ev.T, ev.P)
+    k1, T1, P1, f1 = _by_key(ov.export(), nb)
+    k0, T0, P0, f0 = _by_key(before, nb)
+    assert np.array_equal(k1, k0) and _same_values(T1, T0) and _same_values(P1, P0)
+    moved = np.isin(k0, k_ev)
+    assert np.array_equal(f1[~moved], f0[~moved]) and np.all(f1[moved] == ov.frame)
+
+
+def _refused(fn) -> bool:
+    try:
+        fn()
+    except ValueError:
+        return True
+    return False
+
+
+def pin_import_refuses_duplicates_and_allocated_blocks(lib_path=None):
+    """A block is allocated once: importing an allocated block, a block twice or
+    one outside the grid is refused and changes nothing."""
+    sphere = synth.sphere_sequence(n_frames=2)
+    ov = _fused(sphere, 2, lib_path)
+    e = ov.export()
+    n = ov.n_blocks
+    assert _refused(lambda: ov.import_blocks(e.coords[:1], e.T[:1], e.P[:1]))          # already allocated
+    ev = ov.evict([0, 0, 0], [16, 32, 32])
+    assert len(ev.coords) > 1
+    twice = np.concatenate([ev.coords[:1], ev.coords[:1]])
+    assert _refused(lambda: ov.import_blocks(twice, np.concatenate([ev.T[:1]] * 2), np.concatenate([ev.P[:1]] * 2)))
+    assert _refused(lambda: ov.import_blocks(np.array([[-1, 0, 0]]), ev.T[:1], ev.P[:1]))   # outside the grid
+    assert ov.n_blocks == n - len(ev.coords)
+
+
+def pin_shift_and_its_inverse_restore_the_volume(lib_path=None):
+    """A shift by d moves the origin by 8 s d and evicts the blocks leaving the
+    grid; shifting back and importing them restores the volume."""
+    sphere = synth.sphere_sequence(n_frames=3)
+    ov = _fused(sphere, 3, lib_path)
+    nb = sphere.volume.grid_dim // 8
+    before = ov.export()
+    o0 = ov.origin.copy()
+    d = np.array([4, -3, 2])                      # blocks at x < 4 and z < 2 leave the grid
+    ev = ov.shift(d)
+    assert len(ev.coords) > 0
+    assert np.allclose(ov.origin, o0 + 8 * d * float(np.float32(sphere.volume.voxel_size)), rtol=0, atol=1e-15)
+    mid = ov.export()
+    assert np.all((mid.coords >= 0) & (mid.coords < nb))
+    ev_back = ov.shift(-d)
+    assert len(ev_back.coords) == 0               # nothing leaves on the way back
+    ov.import_blocks(ev.coords, ev.T, ev.P)
+    k1, T1, P1, _ = _by_key(ov.export(), nb)
+    k0, T0, P0, _ = _by_key(before, nb)
+    assert np.array_equal(k1, k0) and _same_values(T1, T0) and _same_values(P1, P0)
+    assert np.allclose(ov.origin, o0, rtol=0, atol=1e-15)
+
+
+def pin_fusing_into_a_shifted_volume_matches_the_unshifted_one(lib_path=None):
+    """Voxel i' = i - 8d of the shifted grid is voxel i of the original: after a
+    shift by d, fusing the remaining frames gives the same T and P at the same
+    world positions (block coordinates moved by -d)."""
+    sphere = synth.sphere_sequence(n_frames=4)
+    nb = sphere.volume.grid_dim // 8
+    ref = _fused(sphere, 4, lib_path)
+    ov = _fused(sphere, 2, lib_path)
+    d = np.array([1, -2, 1])                      # keeps every block of the sphere inside the grid
+    assert len(ov.shift(d).coords) == 0
+    for k in range(2, 4):
+        ov.fuse(sphere.depth[k], sphere.poses[k])
+    a, b = ref.export(), ov.export()
+    b_world = oracle.Export(b.coords + d, b.alloc_frame, b.T, b.P, b.amb)
+    ka, Ta, Pa, _ = _by_key(a, nb)
+    kb, Tb, Pb, _ = _by_key(b_world, nb)
+    assert np.array_equal(ka, kb)
+    amb = _by_key(oracle.Export(a.coords, a.alloc_frame, a.amb.astype(float), a.amb.astype(float), a.amb), nb)[1] > 0
+    amb |= _by_key(oracle.Export(b_world.coords, b.alloc_frame, b.amb.astype(float), b.amb.astype(float), b.amb),
+                  nb)[1] > 0
+    ok = ~amb
+    assert np.array_equal(np.isnan(Ta)[ok], np.isnan(Tb)[ok])
+    both = ok & ~np.isnan(Ta) & ~np.isnan(Tb)
+    delta = float(sphere.volume.truncation)
+    assert both.sum() > 50000
+    assert np.max(np.abs(Ta[both] - Tb[both])) < 1e-9 * delta
+    assert np.max(np.abs(Pa[both] - Pb[both]) / Pa[both]) < 1e-9
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
             pin_alloc_exact_rational, pin_alloc_capacity_and_order, pin_dense_equals_sparse,
             pin_plane_raycast_exact, pin_sphere_raycast_analytic, pin_mlp_gradient_finite_differences,
             pin_mlp_closed_forms, pin_mlp_features_on_planes, pin_mlp_variance_fallback,
-            pin_refined_tk_plane_distances, pin_refined_tk_sphere_distance]
+            pin_refined_tk_plane_distances, pin_refined_tk_sphere_distance,
+            pin_evict_takes_the_blocks_outside_the_box_and_import_restores,
+            pin_import_refuses_duplicates_and_allocated_blocks, pin_shift_and_its_inverse_restore_the_volume,
+            pin_fusing_into_a_shifted_volume_matches_the_unshifted_one]
 
 # the registration oracle is numpy code (oracle/icp.py); its own mutation test
 # plants mistakes in copies of that module

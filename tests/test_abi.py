@@ -100,6 +100,11 @@ def test_null_arguments_are_rejected(lib):
     assert lib.tsdf_export(None, None, None, None, 0, ctypes.byref(n)) == tsdf.ERR_INVALID_ARG
     assert lib.tsdf_quadratic_variance(None, -1, 1e-3, None, None) == tsdf.ERR_INVALID_ARG
     assert lib.tsdf_raycast_trace(None, ctypes.byref(K), pose, None, None) == tsdf.ERR_INVALID_ARG
+    c3 = (ctypes.c_int32 * 3)(0, 0, 0)
+    assert lib.tsdf_get_config(None, None) == tsdf.ERR_INVALID_ARG
+    assert lib.tsdf_evict(None, c3, c3, 0, None, None, None, ctypes.byref(n), None) == tsdf.ERR_INVALID_ARG
+    assert lib.tsdf_shift(None, c3, 0, None, None, None, ctypes.byref(n), None) == tsdf.ERR_INVALID_ARG
+    assert lib.tsdf_import(None, 1, None, None, None, None) == tsdf.ERR_INVALID_ARG
     lib.tsdf_destroy(None)
 
 

@@ -69,6 +69,13 @@ MUTATIONS = [
     ("mlp_variance_exp_sign", "pq * std::exp(out[k])", "pq * std::exp(-out[k])"),
     ("mlp_fallback_limit", "const double lim = std::log(4.0);", "const double lim = std::log(16.0);"),
     ("mlp_first_layer_relu", "t->a1[j] = acc > 0.0 ? acc : 0.0;", "t->a1[j] = acc;"),
+    ("shift_origin_sign", "v.p.origin[r] += (double)((int64_t)M * d[r]) * (double)v.p.voxel_size;",
+     "v.p.origin[r] -= (double)((int64_t)M * d[r]) * (double)v.p.voxel_size;"),
+    ("shift_rekey_sign", "for (int r = 0; r < 3; ++r) b.b[r] -= d[r];", "for (int r = 0; r < 3; ++r) b.b[r] += d[r];"),
+    ("evict_box_upper_inclusive", "if (b.b[r] < lo[r] || b.b[r] >= hi[r]) return true;",
+     "if (b.b[r] < lo[r] || b.b[r] > hi[r]) return true;"),
+    ("import_drops_values", "blk.chi[l] = 0;\n                blk.T[l] = t;", "blk.chi[l] = 0;\n                blk.T[l] = 0.0;"),
+    ("import_allows_allocated", "if (v.index.count(keys.back())) return -1;", "(void)0;"),
 ]
 
 
