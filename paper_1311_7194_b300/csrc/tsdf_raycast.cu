@@ -747,6 +747,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     if (lane == 0 && hits) atomicAdd(&ctr->rays_hit, (unsigned long long)hits);
 }
 
+
 template <int kS, int kTW, int kTH>
 void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
