@@ -505,6 +505,26 @@ __device__ __forceinline__ float zt_minus(float zt, float back, int j) {
     return zt - back + (float)j * (back / (float)kFine);
 }
 
+// One point of a re-scan (the step before a sample that found the field
+// already at or below zero): sq the point's trilinear status, fq its value, zq
+// its camera z; ldef / fa / za the last point (defined, value, z). A + to -
+// pair of defined points brackets the crossing; a - to + pair ends the ray.
+__device__ __forceinline__ void rescan_step(int sq, float fq, float zq, bool& ldef, float& fa, float& za, float* b1,
+                                            float* c1, float* b2, float* c2, bool* push, bool* miss, bool* done) {
+    if (sq != 0) {
+        ldef = false;
+    } else if (ldef && fa > 0.0f && fq <= 0.0f) {
+        *b1 = za; *c1 = fa; *b2 = zq; *c2 = fq;
+        *push = true;
+        *done = true;
+    } else if (ldef && fa < 0.0f && fq > 0.0f) {
+        *miss = true;
+        *done = true;
+    } else {
+        ldef = true; fa = fq; za = zq;
+    }
+}
+
 template <int kS, bool kNarrow>
 __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int* __restrict__ table,
                                                  const typename Codec<kS>::E* __restrict__ T, int pix, float z1,
@@ -591,6 +611,8 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
     // inline.
     bool busy = false, prev_def = false, rays_left = true;
     int pix = 0, it = 0;
+    int rj = -1;        // re-scan substep of the lane's ray, -1 while it marches
+    float ft = 0.f;     // the field at the sample that started the re-scan
     float dqx = 0.f, dqy = 0.f, dqz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f;
     float z = 0.f, zend = 0.f, fprev = 0.f, zl = 0.f, zstep = 0.f;
 
@@ -641,6 +663,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             zl = z;
             zstep = h;
             it = 0;
+            rj = -1;
             busy = true;
         }
         const bool marching = __any_sync(0xffffffffu, busy);
@@ -659,72 +682,76 @@ __global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
             continue;
         }
 
-        // one march sample per busy lane
+        // one march sample per busy lane (a re-scanning lane samples its next substep)
         float f = 0.0f;
         int blk[3] = {0, 0, 0};
-        const int st = busy ? trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(z, dqx, p.q0[0]), __fmaf_rn(z, dqy, p.q0[1]),
-                                            __fmaf_rn(z, dqz, p.q0[2]), &f, blk)
+        const float zs_ = rj >= 0 ? zt_minus(z, zstep, rj) : z;
+        const int st = busy ? trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(zs_, dqx, p.q0[0]),
+                                                            __fmaf_rn(zs_, dqy, p.q0[1]), __fmaf_rn(zs_, dqz, p.q0[2]),
+                                                            &f, blk)
                             : 0;
         bool miss = false, push = false;
         float b1 = 0.f, c1 = 0.f, b2 = 0.f, c2 = 0.f;   // bracket (z1, f1, z2, f2)
         if (busy) {
             bool done = false;
-            if (st == 2) {
+            bool advance = false;   // the march moves on from z (counts an iteration)
+            if (rj >= 0) {
+                // Re-scan substep rj at zs_ (the state holds its own data: prev_def
+                // whether the last substep was defined, fprev / zl its value and
+                // position, zstep the re-scanned length, ft the field at z).
+                rescan_step(st, f, zs_, prev_def, fprev, zl, &b1, &c1, &b2, &c2, &push, &miss, &done);
+                if (!done && ++rj == kFine) {
+                    // the re-scan ends at the sample that started it
+                    rescan_step(0, ft, z, prev_def, fprev, zl, &b1, &c1, &b2, &c2, &push, &miss, &done);
+                    if (!done) {
+                        rj = -1;
+                        prev_def = true;
+                        fprev = ft;
+                        zl = z;
+                        zstep = h;
+                        z += h;
+                        advance = true;
+                    }
+                }
+            } else if (st == 2) {
                 const float inv[3] = {ivx, ivy, ivz};
                 zl = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
                 z = zl + 1e-3f * h;
                 zstep = z - zl;
                 prev_def = false;
+                advance = true;
             } else {
                 const bool def = st == 0;
                 if (def && !prev_def && f <= 0.0f && it > 0) {
-                    // The field starts here already at or below zero: re-scan
-                    // the last step in kFine substeps for a short positive run.
-                    bool ldef = false;
-                    float fa = 0.0f, za = 0.0f;
-                    const float back = fminf(zstep, z - zl);
-                    for (int j = 0; j <= kFine && !done; ++j) {
-                        const float zq = j == kFine ? z : zt_minus(z, back, j);
-                        float fq = f;
-                        const int sq_ = j == kFine ? 0
-                                                   : trilinear<kS, false, kNarrow>(p, table, T, __fmaf_rn(zq, dqx, p.q0[0]),
-                                                                   __fmaf_rn(zq, dqy, p.q0[1]),
-                                                                   __fmaf_rn(zq, dqz, p.q0[2]), &fq, blk);
-                        if (sq_ != 0) {
-                            ldef = false;
-                        } else if (ldef && fa > 0.0f && fq <= 0.0f) {
-                            b1 = za; c1 = fa; b2 = zq; c2 = fq;
-                            push = true;
-                            done = true;
-                        } else if (ldef && fa < 0.0f && fq > 0.0f) {
-                            miss = true;
-                            done = true;
-                        } else {
-                            ldef = true; fa = fq; za = zq;
-                        }
-                    }
-                }
-                if (!done) {
-                    if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
-                        b1 = zl; c1 = fprev; b2 = z; c2 = f;
-                        push = true;
-                        done = true;
-                    } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
-                        miss = true;                      // back face first
-                        done = true;
-                    } else {
-                        prev_def = def;
-                        fprev = f;
-                        zl = z;
-                        zstep = def ? h : 2.0f * h;
-                        z += zstep;
-                    }
+                    // The field starts here already at or below zero: re-scan the
+                    // last step in kFine substeps for a short positive run, one
+                    // substep per iteration, so that the other lanes of the warp
+                    // keep marching meanwhile.
+                    rj = 0;
+                    ft = f;
+                    zstep = fminf(zstep, z - zl);
+                    prev_def = false;
+                } else if (def && prev_def && fprev > 0.0f && f <= 0.0f) {
+                    b1 = zl; c1 = fprev; b2 = z; c2 = f;
+                    push = true;
+                    done = true;
+                } else if (def && prev_def && fprev < 0.0f && f > 0.0f) {
+                    miss = true;                      // back face first
+                    done = true;
+                } else {
+                    prev_def = def;
+                    fprev = f;
+                    zl = z;
+                    zstep = def ? h : 2.0f * h;
+                    z += zstep;
+                    advance = true;
                 }
             }
-            if (!done) {
+            if (advance) {
                 ++it;
                 if (!(it < kMaxMarch && z <= zend)) miss = true;
             }
+            if (done || miss) rj = -1;
         }
         const unsigned pm = __ballot_sync(0xffffffffu, push);
         if (push) {
