@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
 // six independent normal samples are in flight at once.
 constexpr int kRcWarps = 4;          // warps per CTA
 constexpr int kQueue = 64;           // brackets per warp queue (< 32 queued + 32 pushed)
-constexpr int kRefill = 8;           // idle lanes that trigger a refill of the warp
+constexpr int kRefill = 12;         // idle lanes that trigger a refill of the warp
 
 // j-th of the kFine re-scan points of the step (zt - back, zt]
 __device__ __forceinline__ float zt_minus(float zt, float back, int j) {
@@ -581,7 +581,7 @@ __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int
 }
 
 template <int kS, bool kNarrow>
-__global__ void __launch_bounds__(32 * kRcWarps) raycast_persistent_kernel(
+__global__ void __launch_bounds__(32 * kRcWarps, 8) raycast_persistent_kernel(
     const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
     const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
     const unsigned int* __restrict__ occ3, float* __restrict__ depth_out, float* __restrict__ normal_out,
