@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
                                                                     Counters* ctr, int* __restrict__ blk_slot,
                                                                     int4* __restrict__ blocks, long long cap,
                                                                     int frame, int nb, unsigned int* __restrict__ occ2,
-                                                                    unsigned int* __restrict__ occ3, int n2, int n3) {
+                                                                    int n2) {
     pdl_prologue();
     __shared__ unsigned smem[32];
     __shared__ unsigned wsum[kTileThreads / 32];
@@ -161,9 +161,7 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
                 blocks[rank] = make_int4(bx, by, bz, frame);
                 // coarse occupancy used by the raycast to skip empty space
                 const unsigned c2 = (unsigned)(bx / kOcc2) + (unsigned)n2 * ((unsigned)(by / kOcc2) + (unsigned)n2 * (unsigned)(bz / kOcc2));
-                const unsigned c3 = (unsigned)(bx / kOcc3) + (unsigned)n3 * ((unsigned)(by / kOcc3) + (unsigned)n3 * (unsigned)(bz / kOcc3));
                 atomicOr(occ2 + (c2 >> 5), 1u << (c2 & 31u));
-                atomicOr(occ3 + (c3 >> 5), 1u << (c3 & 31u));
             } else {
                 over = true;
             }
@@ -218,7 +216,7 @@ cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParam
     launch_pdl(alloc_count_kernel, dim3(v->n_tiles), dim3(kTileThreads), st,
                reinterpret_cast<const uint4*>(v->newbits), v->tile_sums);
     launch_pdl(alloc_assign_kernel, dim3(v->n_tiles), dim3(kTileThreads), st, v->newbits, v->tile_sums, v->ctr,
-               v->blk_slot, v->blocks, v->cfg.block_capacity, frame, v->nb, v->occ2, v->occ3, v->n2, v->n3);
+               v->blk_slot, v->blocks, v->cfg.block_capacity, frame, v->nb, v->occ2, v->n2);
     launch_pdl(alloc_finalize_kernel, dim3(1), dim3(32), st, v->tile_sums, (int)v->n_tiles, v->ctr,
                v->cfg.block_capacity);
     const int bytes = storage_bytes(v->cfg.storage);

@@ -10,7 +10,7 @@
 //           compacted by moving the last kept blocks into the freed slots (no
 //           slot is both read and written, so one kernel moves them all); the
 //           block table entries of evicted and moved blocks are updated and
-//           the occupancy maps rebuilt.
+//           the occupancy map rebuilt.
 //   shift:  the grid origin moves by whole blocks, so every voxel keeps its
 //           world position; blocks whose new coordinates leave the grid are
 //           evicted as above, the others are re-keyed and the block table is
@@ -106,17 +106,14 @@ __global__ void __launch_bounds__(256) table_gather_kernel(const int* __restrict
         out[i] = table[keys[i]];
 }
 
-// Occupancy bits (cells of 4^3 and 16^3 blocks) of the first n pool blocks.
+// Occupancy bits (cells of 4^3 blocks) of the first n pool blocks.
 __global__ void __launch_bounds__(256) occ_mark_kernel(const int4* __restrict__ blocks, long long n,
-                                                       unsigned int* __restrict__ occ2, unsigned int* __restrict__ occ3,
-                                                       int n2, int n3) {
+                                                       unsigned int* __restrict__ occ2, int n2) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int4 b = blocks[i];
         const unsigned c2 = (unsigned)(b.x / kOcc2) + (unsigned)n2 * ((unsigned)(b.y / kOcc2) + (unsigned)n2 * (unsigned)(b.z / kOcc2));
-        const unsigned c3 = (unsigned)(b.x / kOcc3) + (unsigned)n3 * ((unsigned)(b.y / kOcc3) + (unsigned)n3 * (unsigned)(b.z / kOcc3));
         atomicOr(occ2 + (c2 >> 5), 1u << (c2 & 31u));
-        atomicOr(occ3 + (c3 >> 5), 1u << (c3 & 31u));
     }
 }
 
@@ -208,7 +205,7 @@ cudaError_t launch_put(tsdf_volume* v, const float* inT, const float* inP, long 
 }
 
 // The pool size (committed and "before the last allocation") and the
-// occupancy maps after the block list changed outside an allocation.
+// occupancy map after the block list changed outside an allocation.
 cudaError_t commit_pool(tsdf_volume* v, const std::vector<int4>& blocks, cudaStream_t st) {
     const long long n = (long long)blocks.size();
     cudaError_t e = cudaSuccess;
@@ -216,9 +213,8 @@ cudaError_t commit_pool(tsdf_volume* v, const std::vector<int4>& blocks, cudaStr
     const long long sizes[2] = {n, n};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&v->ctr->n_blocks, sizes, sizeof(sizes), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->occ2, 0, v->occ2_words * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->occ3, 0, v->occ3_words * sizeof(uint32_t), st);
     if (e == cudaSuccess && n > 0) {
-        occ_mark_kernel<<<grid_for(n), 256, 0, st>>>(v->blocks, n, v->occ2, v->occ3, v->n2, v->n3);
+        occ_mark_kernel<<<grid_for(n), 256, 0, st>>>(v->blocks, n, v->occ2, v->n2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -19,7 +19,6 @@ constexpr int kDepthTile = 8;            // depth min / max tiles used by the in
 constexpr int kMaxBatch = 8;             // frames per tsdf_integrate_batch call
 constexpr int kMlpParams = 1985;         // learned-variance network: 27-32-32-1
 constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
-constexpr int kOcc3 = 16;                // occupancy level 3: cells of 16^3 blocks (128 voxels a side)
 
 // Device-resident counters; every data-dependent size lives here so that a
 // sequence of calls needs no host round trip (and can be graph captured).
@@ -88,7 +87,7 @@ struct FrameParams {
     float near_clip, far_clip;
     int width, height;
     int nb, G;
-    int n2, n3;          // occupancy cells per axis at levels 2 and 3
+    int n2;              // occupancy cells per axis (cells of 4^3 blocks)
 };
 
 // Constants of one batched integrate call: K frames fused in order.
@@ -122,9 +121,8 @@ struct tsdf_volume {
     uint32_t* tile_sums;           // [n_tiles]
     int4* blocks;                  // [cap] bx, by, bz, allocation frame
     uint32_t* occ2;                // bit per 4^3-block cell: holds an allocated block
-    uint32_t* occ3;                // bit per 16^3-block cell
-    int32_t n2, n3;                // cells per axis
-    size_t occ2_words, occ3_words;
+    int32_t n2;                    // cells per axis
+    size_t occ2_words;
     void* T;                       // [cap * 512] in the storage format (tsdf_storage)
     float* P;                      // [cap * 512]
     tsdf::VisibleBlock* visible;   // [cap]

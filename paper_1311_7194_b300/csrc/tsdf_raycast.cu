@@ -18,14 +18,13 @@
 //                     with step delta/2 over the trilinear field of T; a sample
 //                     whose lower corner lies in an unallocated block jumps to
 //                     the exit of the largest empty cell around it (the block,
-//                     or a 4^3- or 16^3-block cell empty in the occupancy maps
-//                     kept by the allocation). Where the field becomes defined already at
-//                     or below zero, the last step is re-scanned in delta/32
-//                     substeps for a short positive run. At the first + to - pair
-//                     the crossing is
-//                     refined by Illinois false position (a secant method that keeps
-//                     a bracket) to 0.02 voxel, then
-//                     the normal is the central difference of the field.
+//                     or a 4^3-block cell empty in the occupancy map kept by
+//                     the allocation). Where the field becomes defined already
+//                     at or below zero, the last step is re-scanned in delta/32
+//                     substeps for a short positive run. At the first + to -
+//                     pair the crossing is refined by Illinois false position
+//                     (a secant method that keeps a bracket) to 0.02 voxel,
+//                     then the normal is the central difference of the field.
 // The coarse and fine stages run in one kernel: on sm_103a the register budget
 // that made the paper split them is not the limit, and fusing them avoids a
 // round trip of the per-pixel crossing through memory.
@@ -293,17 +292,18 @@ __device__ __forceinline__ bool occupied(const unsigned int* __restrict__ occ, i
     return (__ldg(occ + (c >> 5)) >> (c & 31u)) & 1u;
 }
 
-// Camera z at which the ray leaves the empty cell around block blk: the largest
-// of (16 blocks)^3, (4 blocks)^3 or the block itself that holds no allocated
-// block (outside the grid counts as empty). inv: 1 / dq per axis (0 where the
-// ray does not move along that axis).
+// Camera z at which the ray leaves the empty cell around block blk: its
+// (4 blocks)^3 cell when the occupancy map marks that cell empty, else the block
+// itself; outside the grid, where nothing is allocated, its (16 blocks)^3 cell.
+// (A 16^3-block occupancy level was measured to cost more than it saves: near
+// surfaces its cells are occupied and its lookup only adds a dependent load.)
+// inv: 1 / dq per axis (0 where the ray does not move along that axis).
 __device__ __forceinline__ float empty_exit(const FrameParams& p, const unsigned int* __restrict__ occ2,
-                                            const unsigned int* __restrict__ occ3, const int blk[3],
-                                            const float inv[3]) {
+                                            const int blk[3], const float inv[3]) {
     const bool inside = blk[0] >= 0 && blk[1] >= 0 && blk[2] >= 0 && blk[0] < p.nb && blk[1] < p.nb && blk[2] < p.nb;
     int shift = 0;   // log2 of blocks per cell side
-    if (!inside || !occupied(occ3, p.n3, blk[0] >> 4, blk[1] >> 4, blk[2] >> 4))
-        shift = 4;
+    if (!inside)
+        shift = 4;   // outside the grid nothing is allocated: a 16^3-block cell
     else if (!occupied(occ2, p.n2, blk[0] >> 2, blk[1] >> 2, blk[2] >> 2))
         shift = 2;
     const float size = (float)(kSide << shift);
@@ -323,7 +323,6 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                                                       const int* __restrict__ table,
                                                       const typename Codec<kS>::E* __restrict__ T,
                                                       const unsigned int* __restrict__ occ2,
-                                                      const unsigned int* __restrict__ occ3,
                                                       float* __restrict__ depth_out, float* __restrict__ normal_out,
                                                       float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
     pdl_prologue();
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(kTW * kTH) raycast_kernel(const FrameParams p,
                 if (st == 2) {
                     trace_add<kTrace>(kTraceSkip);
                     // everything before the empty cell's exit is undefined
-                    zprev_any = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
+                    zprev_any = fmaxf(empty_exit(p, occ2, blk, inv), z);
                     z = zprev_any + 1e-3f * h;
                     zstep = z - zprev_any;
                     prev_def = false;
@@ -584,7 +583,7 @@ template <int kS, bool kNarrow>
 __global__ void __launch_bounds__(32 * kRcWarps, 8) raycast_persistent_kernel(
     const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
     const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
-    const unsigned int* __restrict__ occ3, float* __restrict__ depth_out, float* __restrict__ normal_out,
+    float* __restrict__ depth_out, float* __restrict__ normal_out,
     float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
     pdl_prologue();
     // bracket queue of each warp: pix, z1, f1, z2, f2, dq (x, y, z)
@@ -715,7 +714,7 @@ __global__ void __launch_bounds__(32 * kRcWarps, 8) raycast_persistent_kernel(
                 }
             } else if (st == 2) {
                 const float inv[3] = {ivx, ivy, ivz};
-                zl = fmaxf(empty_exit(p, occ2, occ3, blk, inv), z);
+                zl = fmaxf(empty_exit(p, occ2, blk, inv), z);
                 z = zl + 1e-3f * h;
                 zstep = z - zl;
                 prev_def = false;
@@ -780,7 +779,7 @@ void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
                     float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const dim3 grid((unsigned)((p.width + kTW - 1) / kTW), (unsigned)((p.height + kTH - 1) / kTH));
     launch_pdl(raycast_kernel<kS, kTW, kTH>, grid, dim3(kTW * kTH), st, p, near_, far_, v->blk_slot,
-               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out, normal_out, vertex_out,
+               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, depth_out, normal_out, vertex_out,
                v->ctr);
 }
 
@@ -796,7 +795,7 @@ void launch_persistent(tsdf_volume* v, const FrameParams& p, const unsigned int*
          per_sm < 1))
         per_sm = 1;
     launch_pdl(raycast_persistent_kernel<kS, kNarrow>, dim3(v->num_sms * per_sm), dim3(32 * kRcWarps), st, p, near_,
-               far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, depth_out,
+               far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, depth_out,
                normal_out, vertex_out, v->ctr);
 }
 
@@ -870,7 +869,7 @@ void launch_march_traced(tsdf_volume* v, const FrameParams& p, const unsigned in
                          cudaStream_t st) {
     const dim3 grid((p.width + 15) / 16, (p.height + 7) / 8);
     launch_pdl(raycast_kernel<kS, 16, 8, true>, grid, dim3(128), st, p, near_, far_, v->blk_slot,
-               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, v->occ3, nullptr, nullptr, nullptr, v->ctr);
+               static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, nullptr, nullptr, nullptr, v->ctr);
 }
 
 }  // namespace

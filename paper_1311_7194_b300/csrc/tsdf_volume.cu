@@ -7,7 +7,7 @@
 //                                     is 512 MB: cheap on a 270 GB device, and a
 //                                     lookup is one load with no probing.
 //   blocks     int4  [capacity]       bx, by, bz, allocation frame per slot
-//   occ2, occ3 bitmaps of 4^3- and 16^3-block cells holding any allocated block
+//   occ2       bitmap of 4^3-block cells holding any allocated block
 //                                     (empty-space skipping in the raycast)
 //   T, P       float [capacity * 512] distance and variance, structure of arrays
 //                                     so that raycasting streams T alone
@@ -81,7 +81,6 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->blk_slot);
     cudaFree(v->newbits);
     cudaFree(v->occ2);
-    cudaFree(v->occ3);
     cudaFree(v->tile_sums);
     cudaFree(v->blocks);
     cudaFree(v->T);
@@ -164,7 +163,6 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.nb = v->nb;
     p.G = v->cfg.grid_dim;
     p.n2 = v->n2;
-    p.n3 = v->n3;
     return p;
 }
 
@@ -312,9 +310,7 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     const uint64_t words = (v->n_table + 31) / 32;
     v->n_tiles = (uint32_t)((words + tsdf::kTileWords - 1) / tsdf::kTileWords);
     v->n2 = (int32_t)((nb + tsdf::kOcc2 - 1) / tsdf::kOcc2);
-    v->n3 = (int32_t)((nb + tsdf::kOcc3 - 1) / tsdf::kOcc3);
     v->occ2_words = ((size_t)v->n2 * v->n2 * v->n2 + 31) / 32;
-    v->occ3_words = ((size_t)v->n3 * v->n3 * v->n3 + 31) / 32;
     v->host_error = TSDF_OK;
     v->lc = tsdf::LaunchConfig{4, 12, 16, 8, 0};
     cudaError_t e = cudaGetDevice(&v->device);
@@ -330,7 +326,6 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     ok = ok && cudaMalloc(&v->tile_sums, (size_t)v->n_tiles * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->blocks, cap * sizeof(int4)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->occ2, v->occ2_words * sizeof(uint32_t)) == cudaSuccess;
-    ok = ok && cudaMalloc(&v->occ3, v->occ3_words * sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->T, cap * tsdf::kBlockVoxels * tsdf::storage_bytes(c.storage)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->P, cap * tsdf::kBlockVoxels * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&v->visible, cap * sizeof(tsdf::VisibleBlock)) == cudaSuccess;
@@ -346,7 +341,6 @@ tsdf_status tsdf_create_ex(const tsdf_config* cfg, tsdf_volume** out) {
     if (e == cudaSuccess) e = cudaMemset(v->newbits, 0, (size_t)v->n_tiles * tsdf::kTileWords * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(v->ctr, 0, sizeof(Counters));
     if (e == cudaSuccess) e = cudaMemset(v->occ2, 0, v->occ2_words * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(v->occ3, 0, v->occ3_words * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_all(v);
@@ -382,7 +376,6 @@ tsdf_status tsdf_reset(tsdf_volume* v, void* stream) {
     cudaError_t e = cudaMemsetAsync(v->blk_slot, 0xff, v->n_table * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->ctr, 0, sizeof(Counters), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->occ2, 0, v->occ2_words * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->occ3, 0, v->occ3_words * sizeof(uint32_t), st);
     if (e != cudaSuccess) return fail_cuda(v, e);
     v->frame = 0;
     v->host_error = TSDF_OK;
