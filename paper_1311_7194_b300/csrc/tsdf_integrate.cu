@@ -1,6 +1,9 @@
 // Measurement integration (section "Integration of Measurements", Alg. 3).
 //
-//   depth_tiles:      per 8x8-pixel tile, the min and max valid measured depth.
+//   depth_tiles:      per 8x8-pixel tile, the min and max valid measured depth;
+//                     per pixel, the measurement map (D, p_k): D is NaN where
+//                     the pixel gives no measurement (invalid depth or variance),
+//                     so a single band test |D - z| <= delta rejects it too.
 //   cull_kernel:      one thread per allocated block; keeps blocks whose box can
 //                     project into the image within the depth range where a
 //                     voxel can have |T_k| <= delta, and whose projected footprint
@@ -91,10 +94,14 @@ __device__ __forceinline__ void reset_frame_counters(Counters* ctr) {
 }
 
 // Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
-// the tile has none. One warp per tile, two pixels per lane. Thread 0 also
-// resets the call's counters when `reset` is given.
-__global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth, FrameParams p,
-                                                          float2* __restrict__ tiles, Counters* __restrict__ reset) {
+// the tile has none. Per pixel: meas = (D, p_k), p_k from the variance map when
+// one is given, else the quadratic model (a D^2)^2; D becomes NaN when it is not
+// a valid depth or p_k is not a positive finite variance. One warp per tile, two
+// pixels per lane. Thread 0 also resets the call's counters when `reset` is given.
+__global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth,
+                                                          const float* __restrict__ var, FrameParams p,
+                                                          float2* __restrict__ tiles, float2* __restrict__ meas,
+                                                          Counters* __restrict__ reset) {
     pdl_prologue();
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
@@ -109,11 +116,22 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restric
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (u + k < p.width) {
-                    const float d = __ldg(depth + (size_t)v * p.width + u + k);
-                    if (depth_ok(d, p.depth_min, p.depth_max)) {
+                    const size_t pix = (size_t)v * p.width + u + k;
+                    const float d = __ldg(depth + pix);
+                    const bool valid = depth_ok(d, p.depth_min, p.depth_max);
+                    if (valid) {
                         lo = fminf(lo, d);
                         hi = fmaxf(hi, d);
                     }
+                    float pv;
+                    if (var) {
+                        pv = __ldg(var + pix);
+                    } else {
+                        const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
+                        pv = __fmul_rn(sg, sg);
+                    }
+                    const bool use = valid && pv > 0.0f && pv <= 3.0e38f;
+                    meas[pix] = make_float2(use ? d : __int_as_float(0x7fc00000), pv);
                 }
             }
         }
@@ -320,39 +338,31 @@ __device__ __forceinline__ float refine_tk(const FrameParams& p, const float* __
 // The batched kernel needs it (an entry of a frame the block cannot reach
 // carries an empty range); in the single-frame kernel the range from the
 // depth tiles rejects few voxels, and the band test alone decides.
-template <bool kVarMap, bool kRefine, bool kZRange = true>
+template <bool kRefine, bool kZRange = true>
 __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
-                                        float zr, const float* __restrict__ depth, const float* __restrict__ var,
+                                        float zr, const float2* __restrict__ meas, const float* __restrict__ depth,
                                         float* Tk, float* pk) {
     const float zs = __fmaf_rn(lx, p.cs[6], zr);
     const float z = __fadd_rn(vb.o[2], zs);
-    if (kZRange ? !(z > 1e-30f && z >= vb.zlo && z <= vb.zhi) : !(z > 1e-30f)) return false;
     const float x = __fmaf_rn(lx, p.cs[0], xr);
     const float y = __fmaf_rn(lx, p.cs[3], yr);
     const float rz = rcp_newton(z);
     const float uf = __fmaf_rn(p.fx, __fmul_rn(x, rz), p.cxh);   // u + 1/2
     const float vf = __fmaf_rn(p.fy, __fmul_rn(y, rz), p.cyh);
-    // nearest pixel: floor(u + 1/2) in [0, W) (z > 1e-30 keeps u, v finite; a
-    // value beyond the int range saturates and fails the unsigned test)
+    // nearest pixel: floor(u + 1/2) in [0, W). Without a branch: a voxel that
+    // fails a test still loads pixel 0 and is rejected by the flag (for
+    // z <= 1e-30, u and v may be infinite or NaN; the flag drops them).
     const int ui = __float2int_rd(uf), vi = __float2int_rd(vf);
-    if ((unsigned)ui >= (unsigned)p.width || (unsigned)vi >= (unsigned)p.height) return false;
-    const int pix = vi * p.width + ui;
-    const float D = __ldg(depth + pix);
-    // the band test first: most voxels that get here fail it
-    const float t = __fsub_rn(__fsub_rn(D, vb.o[2]), zs);
-    if (!(fabsf(t) <= p.delta)) return false;
-    if (!depth_ok(D, p.depth_min, p.depth_max)) return false;
-    float pv;
-    if (kVarMap) {
-        pv = __ldg(var + pix);
-    } else {
-        const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, D), D);
-        pv = __fmul_rn(sg, sg);
-    }
-    if (!(pv > 0.0f && pv <= 3.0e38f)) return false;
-    *Tk = kRefine ? refine_tk(p, depth, x, y, vb.o[2], zs, uf - 0.5f, vf - 0.5f, t) : t;
-    *pk = pv;
-    return true;
+    bool ok = (z > 1e-30f) & ((unsigned)ui < (unsigned)p.width) & ((unsigned)vi < (unsigned)p.height);
+    if (kZRange) ok &= (z >= vb.zlo) & (z <= vb.zhi);
+    const int pix = ok ? vi * p.width + ui : 0;
+    const float2 m = __ldg(meas + pix);               // (D or NaN, p_k)
+    const float t = __fsub_rn(__fsub_rn(m.x, vb.o[2]), zs);
+    ok &= fabsf(t) <= p.delta;                        // false for a NaN D
+    *Tk = t;
+    if (kRefine && ok) *Tk = refine_tk(p, depth, x, y, vb.o[2], zs, uf - 0.5f, vf - 0.5f, t);
+    *pk = m.y;
+    return ok;
 }
 
 // One measurement into one voxel, chi is NaN; kRule is a tsdf_update_rule.
@@ -383,13 +393,13 @@ __device__ __forceinline__ void update(const FrameParams& p, float& T, float& P,
     if (fabsf(T) > p.delta) T = __int_as_float(0x7fc00000);
 }
 
-template <bool kVarMap, int kS, int kVPT, int kRule, bool kRefine>
+template <int kS, int kVPT, int kRule, bool kRefine>
 __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Counters* __restrict__ ctr,
                                                                         const VisibleBlock* __restrict__ vis,
                                                                         typename Codec<kS>::E* __restrict__ T,
                                                                         float* __restrict__ P,
-                                                                        const float* __restrict__ depth,
-                                                                        const float* __restrict__ var, FrameParams p) {
+                                                                        const float2* __restrict__ meas,
+                                                                        const float* __restrict__ depth, FrameParams p) {
     pdl_prologue();
     static_assert(kVPT == 4 || kVPT == 8, "a thread owns 4 or 8 consecutive voxels of an x row");
     const unsigned nvis = ctr->n_visible;
@@ -407,7 +417,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
         bool any = false;
 #pragma unroll
         for (int e = 0; e < kVPT; ++e) {
-            ok[e] = measure<kVarMap, kRefine, false>(p, vb, lx0 + (float)e, xr, yr, zr, depth, var, &tk[e], &pk[e]);
+            ok[e] = measure<kRefine, false>(p, vb, lx0 + (float)e, xr, yr, zr, meas, depth, &tk[e], &pk[e]);
             any |= ok[e];
         }
         if (!any) continue;
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
 // before the block's allocation - and stored once. Same measurement and update
 // functions as integrate_kernel, so the result equals K sequential calls bit
 // for bit.
-template <bool kVarMap, int kS, int kRule, bool kRefine>
+template <int kS, int kRule, bool kRefine>
 __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
                                                                             const VisibleBlock* __restrict__ vis,
                                                                             const int4* __restrict__ blocks,
@@ -464,6 +474,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
         for (int k = max(first, 0); k < bp.K; ++k) {
             const FrameParams& p = bp.fp[k];
             const VisibleBlock vb = ve[k];
+            if (!(vb.zlo <= vb.zhi)) continue;             // a frame the block cannot reach
             const float xr = __fmaf_rn(ly, p.cs[1], __fmaf_rn(lz, p.cs[2], vb.o[0]));
             const float yr = __fmaf_rn(ly, p.cs[4], __fmaf_rn(lz, p.cs[5], vb.o[1]));
             const float zr = __fmaf_rn(ly, p.cs[7], __fmaf_rn(lz, p.cs[8], vb.oz_lo));
@@ -472,8 +483,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             bool any = false;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                ok[e] = measure<kVarMap, kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, bp.depth[k], bp.var[k], &tk[e],
-                                                  &pk[e]);
+                ok[e] = measure<kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, bp.meas[k], bp.depth[k], &tk[e], &pk[e]);
                 any |= ok[e];
             }
             if (!any) continue;
@@ -504,56 +514,44 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
 
 
 template <int kS, int kVPT, int kRule, bool kRefine>
-void launch_integrate_f(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
-                        cudaStream_t st) {
+void launch_integrate_f(tsdf_volume* v, const float* depth, const FrameParams& p, unsigned grid, cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
     constexpr int threads = kBlockVoxels / kVPT;
-    if (var)
-        launch_pdl(integrate_kernel<true, kS, kVPT, kRule, kRefine>, dim3(grid), dim3(threads), st, v->ctr,
-                   v->visible, T, v->P, depth, var, p);
-    else
-        launch_pdl(integrate_kernel<false, kS, kVPT, kRule, kRefine>, dim3(grid), dim3(threads), st, v->ctr,
-                   v->visible, T, v->P, depth, var, p);
+    launch_pdl(integrate_kernel<kS, kVPT, kRule, kRefine>, dim3(grid), dim3(threads), st, v->ctr, v->visible, T,
+               v->P, static_cast<const float2*>(v->meas), depth, p);
 }
 
 // The refined measurement is instantiated for 4 voxels per thread only.
 template <int kS, int kVPT, int kRule>
-void launch_integrate_r(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
-                        cudaStream_t st) {
+void launch_integrate_r(tsdf_volume* v, const float* depth, const FrameParams& p, unsigned grid, cudaStream_t st) {
     if (p.refine_steps > 0)
-        launch_integrate_f<kS, 4, kRule, true>(v, depth, var, p, grid, st);
+        launch_integrate_f<kS, 4, kRule, true>(v, depth, p, grid, st);
     else
-        launch_integrate_f<kS, kVPT, kRule, false>(v, depth, var, p, grid, st);
+        launch_integrate_f<kS, kVPT, kRule, false>(v, depth, p, grid, st);
 }
 
 template <int kS, int kVPT>
-void launch_integrate_v(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
-                        cudaStream_t st) {
+void launch_integrate_v(tsdf_volume* v, const float* depth, const FrameParams& p, unsigned grid, cudaStream_t st) {
     switch (v->cfg.update_rule) {
-        case TSDF_UPDATE_AVERAGE: launch_integrate_r<kS, kVPT, TSDF_UPDATE_AVERAGE>(v, depth, var, p, grid, st); break;
-        case TSDF_UPDATE_WEIGHTED: launch_integrate_r<kS, kVPT, TSDF_UPDATE_WEIGHTED>(v, depth, var, p, grid, st); break;
-        default: launch_integrate_r<kS, kVPT, TSDF_UPDATE_KALMAN>(v, depth, var, p, grid, st); break;
+        case TSDF_UPDATE_AVERAGE: launch_integrate_r<kS, kVPT, TSDF_UPDATE_AVERAGE>(v, depth, p, grid, st); break;
+        case TSDF_UPDATE_WEIGHTED: launch_integrate_r<kS, kVPT, TSDF_UPDATE_WEIGHTED>(v, depth, p, grid, st); break;
+        default: launch_integrate_r<kS, kVPT, TSDF_UPDATE_KALMAN>(v, depth, p, grid, st); break;
     }
 }
 
 template <int kS>
-void launch_integrate_s(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, unsigned grid,
-                        cudaStream_t st) {
+void launch_integrate_s(tsdf_volume* v, const float* depth, const FrameParams& p, unsigned grid, cudaStream_t st) {
     if (v->lc.integrate_vpt == 8)
-        launch_integrate_v<kS, 8>(v, depth, var, p, grid, st);
+        launch_integrate_v<kS, 8>(v, depth, p, grid, st);
     else
-        launch_integrate_v<kS, 4>(v, depth, var, p, grid, st);
+        launch_integrate_v<kS, 4>(v, depth, p, grid, st);
 }
 
 template <int kS, int kRule, bool kRefine>
 void launch_integrate_batch_f(tsdf_volume* v, const BatchParams& bp, unsigned grid, cudaStream_t st) {
     auto* T = static_cast<typename Codec<kS>::E*>(v->T);
-    if (bp.var[0])
-        launch_pdl(integrate_batch_kernel<true, kS, kRule, kRefine>, dim3(grid), dim3(kIntegrateThreads), st,
-                   v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
-    else
-        launch_pdl(integrate_batch_kernel<false, kS, kRule, kRefine>, dim3(grid), dim3(kIntegrateThreads), st,
-                   v->ctr, v->visible_batch, v->blocks, T, v->P, bp);
+    launch_pdl(integrate_batch_kernel<kS, kRule, kRefine>, dim3(grid), dim3(kIntegrateThreads), st, v->ctr,
+               v->visible_batch, v->blocks, T, v->P, bp);
 }
 
 template <int kS, int kRule>
@@ -583,13 +581,13 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
         if (e != cudaSuccess) return e;
         var = v->var_map;
     }
-    launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, depth, p, v->dtiles, v->ctr);
+    launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, v->dtiles, v->meas, v->ctr);
     launch_pdl(cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
-        case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, var, p, grid, st); break;
-        case TSDF_STORAGE_SNORM16: launch_integrate_s<TSDF_STORAGE_SNORM16>(v, depth, var, p, grid, st); break;
-        default: launch_integrate_s<TSDF_STORAGE_F32>(v, depth, var, p, grid, st); break;
+        case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, p, grid, st); break;
+        case TSDF_STORAGE_SNORM16: launch_integrate_s<TSDF_STORAGE_SNORM16>(v, depth, p, grid, st); break;
+        default: launch_integrate_s<TSDF_STORAGE_F32>(v, depth, p, grid, st); break;
     }
     return cudaGetLastError();
 }
@@ -604,9 +602,12 @@ cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cud
             bp.var[k] = vk;
         }
     }
-    for (int k = 0; k < bp.K; ++k)
-        launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, bp.depth[k], bp.fp[k],
-                   v->dtiles_batch + k * v->dtiles_batch_stride, k == 0 ? v->ctr : nullptr);
+    for (int k = 0; k < bp.K; ++k) {
+        float2* mk = v->meas_batch + k * v->var_batch_stride;
+        launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, bp.depth[k], bp.var[k], bp.fp[k],
+                   v->dtiles_batch + k * v->dtiles_batch_stride, mk, k == 0 ? v->ctr : nullptr);
+        bp.meas[k] = mk;
+    }
     launch_pdl(cull_batch_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, bp, v->dtiles_batch,
                v->dtiles_batch_stride, v->visible_batch);
     const unsigned grid = (unsigned)v->num_sms * 12;

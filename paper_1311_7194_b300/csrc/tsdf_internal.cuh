@@ -95,6 +95,7 @@ struct BatchParams {
     FrameParams fp[kMaxBatch];
     const float* depth[kMaxBatch];
     const float* var[kMaxBatch];
+    const float2* meas[kMaxBatch];   // per-pixel measurement maps written by depth_tiles
     int K;
     int f0;              // frame counter of the batch's first frame
 };
@@ -137,8 +138,10 @@ struct tsdf_volume {
     int64_t dtiles_batch_stride;
     void* mlp_w;                   // learned-variance weights (bfloat16, device) or null
     float* var_map;                // variance map made by the network for one frame
-    int64_t var_cap;
+    float2* meas;                  // per pixel (depth, or NaN when it gives no measurement; p_k)
+    int64_t var_cap;               // pixels of var_map and meas
     float* var_batch;              // [kMaxBatch * var_batch_stride]
+    float2* meas_batch;            // [kMaxBatch * var_batch_stride]
     int64_t var_batch_stride;
     double* icp_part;              // registration partial sums (lazily allocated)
     void* mesh_scratch;            // marching cubes: per-block counts and offsets (lazily allocated)
@@ -189,7 +192,7 @@ AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
 FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);
 
 __device__ __forceinline__ bool depth_ok(float d, float dmin, float dmax) {
-    return isfinite(d) && d > 0.0f && d >= dmin && d <= dmax;
+    return (fabsf(d) < __int_as_float(0x7f800000)) & (d > 0.0f) & (d >= dmin) & (d <= dmax);
 }
 
 __device__ __forceinline__ unsigned int warp_sum(unsigned int x) {

@@ -94,7 +94,9 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->dtiles_batch);
     cudaFree(v->mlp_w);
     cudaFree(v->var_map);
+    cudaFree(v->meas);
     cudaFree(v->var_batch);
+    cudaFree(v->meas_batch);
     cudaFree(v->icp_part);
     cudaFree(v->mesh_scratch);
 }
@@ -182,11 +184,14 @@ cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t
         if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
         if (e == cudaSuccess) v->dtiles_cap = ntiles;
     }
-    if (e == cudaSuccess && npix > v->var_cap) {   // variance map of the learned model
+    if (e == cudaSuccess && npix > v->var_cap) {   // variance map of the learned model, measurement map
         e = cudaFree(v->var_map);
+        if (e == cudaSuccess) e = cudaFree(v->meas);
         v->var_map = nullptr;
+        v->meas = nullptr;
         v->var_cap = 0;
         if (e == cudaSuccess) e = cudaMalloc(&v->var_map, (size_t)npix * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v->meas, (size_t)npix * sizeof(float2));
         if (e == cudaSuccess) v->var_cap = npix;
     }
     return e;
@@ -208,9 +213,12 @@ cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t 
     }
     if (e == cudaSuccess && npix > v->var_batch_stride) {
         e = cudaFree(v->var_batch);
+        if (e == cudaSuccess) e = cudaFree(v->meas_batch);
         v->var_batch = nullptr;
+        v->meas_batch = nullptr;
         v->var_batch_stride = 0;
         if (e == cudaSuccess) e = cudaMalloc(&v->var_batch, (size_t)npix * kMaxBatch * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v->meas_batch, (size_t)npix * kMaxBatch * sizeof(float2));
         if (e == cudaSuccess) v->var_batch_stride = npix;
     }
     return e;
