@@ -231,12 +231,12 @@ def _sha(path):
 # when that source changes.
 NCU_TRAFFIC = {
     # frames 100-109, 10 launches each of depth_tiles + cull + integrate:
-    # 2096.9 MB over 76.55 M voxel updates
-    "integrate": {"sha": "aef8d58e3d54a5a1", "bytes_per_unit": 27.39},
+    # 2141.8 MB over 76.55 M voxel updates
+    "integrate": {"sha": "49b71f4456e18a40", "bytes_per_unit": 27.98},
     # same frames, 10 launches each of clear + range cull + raster +
-    # persistent raycast: 1017.5 MB against 816.0 MB of traced unique bytes,
+    # persistent raycast: 1016.3 MB against 816.0 MB of traced unique bytes,
     # i.e. DRAM bytes per algorithmic byte
-    "raycast": {"sha": "68111240e633b1ca", "bytes_per_unit": 1.2469},
+    "raycast": {"sha": "68111240e633b1ca", "bytes_per_unit": 1.2454},
 }
 STAGE_SOURCES = {"integrate": "tsdf_integrate.cu", "raycast": "tsdf_raycast.cu"}
 TRACE_EVERY = 10
