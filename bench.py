@@ -232,7 +232,7 @@ def _sha(path):
 NCU_TRAFFIC = {
     # frames 100-109, 10 launches each of depth_tiles + cull + integrate:
     # 2141.8 MB over 76.55 M voxel updates
-    "integrate": {"sha": "49b71f4456e18a40", "bytes_per_unit": 27.98},
+    "integrate": {"sha": "bae62bb20ea903a0", "bytes_per_unit": 27.98},
     # same frames, 10 launches each of clear + range cull + raster +
     # persistent raycast: 1016.3 MB against 816.0 MB of traced unique bytes,
     # i.e. DRAM bytes per algorithmic byte

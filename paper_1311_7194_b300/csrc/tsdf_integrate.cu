@@ -28,9 +28,10 @@
 //
 // In the batched kernel a voxel whose camera z lies outside the block's reach of
 // the band (the depth range under the block's footprint widened by delta, from
-// the cull) is rejected before any projection: it cannot have |T_k| <= delta.
-// That range is what marks the frames of a batch a block cannot reach; for a
-// single frame it rejects few voxels, and the projection goes first.
+// the cull) is rejected by its flag: it cannot have |T_k| <= delta. An empty
+// range marks a frame of the batch the block cannot reach, and the kernel skips
+// that frame for the whole block. For a single frame the range rejects few
+// voxels and is not tested.
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -334,10 +335,9 @@ __device__ __forceinline__ float refine_tk(const FrameParams& p, const float* __
     return dist < 0.0f ? t0 : side * dist;
 }
 
-// kZRange: reject voxels outside the entry's camera-z range [zlo, zhi] first.
-// The batched kernel needs it (an entry of a frame the block cannot reach
-// carries an empty range); in the single-frame kernel the range from the
-// depth tiles rejects few voxels, and the band test alone decides.
+// kZRange: voxels outside the entry's camera-z range [zlo, zhi] also fail the
+// flag (batched kernel); in the single-frame kernel that range rejects few
+// voxels, and the band test alone decides.
 template <bool kRefine, bool kZRange = true>
 __device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
                                         float zr, const float2* __restrict__ meas, const float* __restrict__ depth,
