@@ -324,18 +324,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(F)] for _ in range(args.steps)]
     t0.record(stream)
     for s in range(args.steps):
-        step(ev[s])
+        step()
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1000.0
     st = vol.stats()
     vol.check()
+    # Stage times (the rooflines' launch durations): the same steps timed again
+    # with event nodes at the stage boundaries of every frame. They sit between
+    # the stages' kernels, so they cut the programmatic-launch overlap there;
+    # the headline region above carries none.
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(F)] for _ in range(args.steps)]
+    for s in range(args.steps):
+        step(ev[s])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
     stage = np.zeros(3)
     for s in range(args.steps):
         for k in range(F):
@@ -396,7 +403,9 @@ def run_ours(args):
                        "launch": "one CUDA graph per frame" if args.mode == "graph" else "one C-ABI call per stage",
                        "launch_shape": tuned or vol.launch_config(),
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step"},
+                       "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step",
+                       "stage_timing": "stage_ms_per_step and the rooflines' durations: a second timed pass of the "
+                                       "same steps with CUDA event nodes at every stage boundary"},
             "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,
             "rays_per_s": rays_per_step * args.steps * world / elapsed_max,
             "stage_ms_per_step": {"allocate": stage_ms_per_step[0], "integrate": stage_ms_per_step[1],

@@ -48,7 +48,7 @@ typedef enum {
     TSDF_ERR_HASH_FULL = 3,     /* reserved: the dense block table never fills */
     TSDF_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
     TSDF_ERR_NOT_READY = 5,     /* reserved */
-    TSDF_ERR_OUT_OF_MEMORY = 6  /* device allocation failed in tsdf_create* */
+    TSDF_ERR_OUT_OF_MEMORY = 6  /* device allocation failed (tsdf_create*, host-input staging) */
 } tsdf_status;
 
 /* How T is held in the pool (P is always float32 and all arithmetic float32;
@@ -383,6 +383,19 @@ tsdf_status tsdf_graph_create(tsdf_volume* vol, int32_t K, const tsdf_intrinsics
 tsdf_status tsdf_graph_launch(tsdf_graph* g, const float* const* depth, const float* const* variance,
                               const double* poses_wc, float* depth_out, float* normal_out,
                               float* vertex_out, void* stream);
+/* The same step from host depth maps. depth_host: host array of K host
+ * pointers, each a width x height float32 map (page-locked memory lets the copy
+ * overlap the previous step's kernels; pageable memory works but copies
+ * synchronously). The maps are copied into one of two library-owned device
+ * staging sets on a private stream, and the graph runs on `stream` once the
+ * copy is done; the sets alternate per call, so a map may be reused by the
+ * caller once this call's work on `stream` has completed. Variance: the
+ * volume's own (quadratic, or the installed network). Outputs as
+ * tsdf_graph_launch (device pointers). The first call allocates the staging
+ * sets (2 K width x height floats) and may synchronise. Errors as
+ * tsdf_graph_launch, and TSDF_ERR_OUT_OF_MEMORY for the staging sets. */
+tsdf_status tsdf_graph_launch_host(tsdf_graph* g, const float* const* depth_host, const double* poses_wc,
+                                   float* depth_out, float* normal_out, float* vertex_out, void* stream);
 /* Number of graph instantiations so far (1 after the first step when every
  * update succeeded); -1 for NULL. */
 int64_t tsdf_graph_instantiations(const tsdf_graph* g);

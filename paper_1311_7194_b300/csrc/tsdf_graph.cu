@@ -13,6 +13,12 @@
 // Every size the kernels need lives in device counters, which is what
 // makes the step capturable: no host round trip, no allocation (buffers are
 // sized by tsdf_graph_create).
+//
+// Host-input steps (tsdf_graph_launch_host) copy the step's depth maps into one
+// of two device staging sets on a private copy stream and make the caller's
+// stream wait for that copy only. The sets alternate per step, and a set is
+// overwritten only after the step that read it (two steps back) has run, so
+// the copy of step n + 1 overlaps the kernels of step n.
 #include <cstdlib>
 #include <cstring>
 
@@ -27,7 +33,49 @@ struct tsdf_graph {
     int64_t steps;
     int64_t instantiations;
     cudaEvent_t events[4];     // optional stage-boundary events for the next launch
+    // host-input steps: two staging sets of K depth maps, filled on `copy`
+    cudaStream_t copy;
+    float* stage;              // [2][K][width * height]
+    cudaEvent_t copied[2];     // the set's copy is done
+    cudaEvent_t done[2];       // the step that read the set has run
+    int done_valid[2];
+    int64_t host_steps;
 };
+
+namespace {
+
+void free_host_staging(tsdf_graph* g) {
+    if (g->copy) cudaStreamSynchronize(g->copy);
+    for (int b = 0; b < 2; ++b) {
+        if (g->copied[b]) cudaEventDestroy(g->copied[b]);
+        if (g->done[b]) cudaEventDestroy(g->done[b]);
+        g->copied[b] = g->done[b] = nullptr;
+        g->done_valid[b] = 0;
+    }
+    if (g->stage) cudaFree(g->stage);
+    if (g->copy) cudaStreamDestroy(g->copy);
+    g->stage = nullptr;
+    g->copy = nullptr;
+}
+
+// Created on the first host-input step (may allocate and synchronise).
+tsdf_status ensure_host_staging(tsdf_graph* g) {
+    if (g->stage) return TSDF_OK;
+    const size_t npix = (size_t)g->intr.width * g->intr.height;
+    cudaError_t e = cudaStreamCreateWithFlags(&g->copy, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&g->copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&g->stage, 2 * (size_t)g->K * npix * sizeof(float));
+    if (e == cudaSuccess) return TSDF_OK;
+    const tsdf_status s = e == cudaErrorMemoryAllocation ? TSDF_ERR_OUT_OF_MEMORY : TSDF_ERR_CUDA;
+    cudaGetLastError();
+    free_host_staging(g);
+    return s;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -55,6 +103,7 @@ tsdf_status tsdf_graph_create(tsdf_volume* v, int32_t K, const tsdf_intrinsics* 
 void tsdf_graph_destroy(tsdf_graph* g) {
     if (!g) return;
     if (g->vol && g->vol->last_stream) cudaStreamSynchronize(g->vol->last_stream);
+    free_host_staging(g);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     cudaStreamDestroy(g->cap);
     std::free(g);
@@ -139,6 +188,46 @@ tsdf_status tsdf_graph_launch(tsdf_graph* g, const float* const* depth, const fl
     v->last_stream = st;
     v->frame += K;
     ++g->steps;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_graph_launch_host(tsdf_graph* g, const float* const* depth_host, const double* poses_wc,
+                                   float* depth_out, float* normal_out, float* vertex_out, void* stream) {
+    if (!g || !depth_host || !poses_wc) return TSDF_ERR_INVALID_ARG;
+    const int K = g->K;
+    for (int k = 0; k < K; ++k)
+        if (!depth_host[k] || !tsdf::pose_valid(poses_wc + 16 * k)) return TSDF_ERR_INVALID_ARG;
+    tsdf_status s = ensure_host_staging(g);
+    if (s != TSDF_OK) return s;
+    tsdf_volume* v = g->vol;
+    const size_t npix = (size_t)g->intr.width * g->intr.height;
+    const int b = (int)(g->host_steps & 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    // the set is free once the step that read it (two host steps back) has run
+    if (g->done_valid[b]) e = cudaStreamWaitEvent(g->copy, g->done[b], 0);
+    const float* dev[tsdf::kMaxBatch];
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        float* d = g->stage + ((size_t)b * K + k) * npix;
+        e = cudaMemcpyAsync(d, depth_host[k], npix * sizeof(float), cudaMemcpyHostToDevice, g->copy);
+        dev[k] = d;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(g->copied[b], g->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->copied[b], 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;
+        return TSDF_ERR_CUDA;
+    }
+    s = tsdf_graph_launch(g, dev, nullptr, poses_wc, depth_out, normal_out, vertex_out, stream);
+    if (s != TSDF_OK) return s;
+    e = cudaEventRecord(g->done[b], st);
+    if (e != cudaSuccess) {
+        if (v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;
+        return TSDF_ERR_CUDA;
+    }
+    g->done_valid[b] = 1;
+    ++g->host_steps;
     return TSDF_OK;
 }
 

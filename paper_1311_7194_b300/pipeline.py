@@ -4,9 +4,11 @@ this library, so each frame is fused at its given pose and the fused model is
 raycast at that pose for the next frame's alignment).
 
 ``FusionPipeline.step`` enqueues allocate -> integrate -> raycast for one depth
-map already on the device; ``step_host`` first copies a pinned host depth map
-into one of two device staging buffers on the same stream. Nothing here
-synchronises: results are read by the caller when needed.
+map already on the device; ``step_host`` starts from a host depth map: with a
+graph, the library copies it (tsdf_graph_launch_host: a private copy stream and
+two staging sets, so the copy overlaps the previous step); without one, it is
+copied into one of two device staging buffers on the step's stream. Nothing
+here synchronises: results are read by the caller when needed.
 """
 from __future__ import annotations
 
@@ -47,7 +49,11 @@ class FusionPipeline:
         self.volume.raycast(self.intr, pose, out=self.maps, stream=stream)
 
     def step_host(self, depth_host: torch.Tensor, pose, stream=None):
-        """Copy a (pinned) host depth map to the device, then ``step``."""
+        """``step`` from a (pinned) host depth map; keep it unchanged until the
+        step's work on the stream has completed."""
+        if self.graph is not None:
+            self.graph.launch_host([depth_host], [pose], self.maps, stream)
+            return
         buf = self._staging[self._k & 1]
         self._k += 1
         s = torch.cuda.current_stream() if stream is None else stream

@@ -24,7 +24,7 @@ UPDATE_KALMAN, UPDATE_AVERAGE, UPDATE_WEIGHTED = 0, 1, 2      # tsdf_update_rule
 EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
             "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_icp_params_default", "tsdf_icp", "tsdf_icp_sums",
-            "tsdf_icp_solve", "tsdf_mesh", "tsdf_mesh_case", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_instantiations",
+            "tsdf_icp_solve", "tsdf_mesh", "tsdf_mesh_case", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_launch_host", "tsdf_graph_instantiations",
             "tsdf_graph_set_events", "tsdf_graph_destroy", "tsdf_get_launch_config", "tsdf_set_launch_config",
             "tsdf_autotune", "tsdf_mlp_param_count", "tsdf_set_variance_mlp", "tsdf_mlp_variance",
             "tsdf_mlp_features", "tsdf_mlp_harvest", "tsdf_mlp_forward", "tsdf_mlp_loss_grad", "tsdf_mlp_adam",
@@ -144,6 +144,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_int32)]),
         "tsdf_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Intrinsics), ctypes.POINTER(_P)]),
         "tsdf_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
+        "tsdf_graph_launch_host": (ctypes.c_int, [_P, ctypes.POINTER(_P), _PD, _P, _P, _P, _P]),
         "tsdf_graph_instantiations": (ctypes.c_int64, [_P]),
         "tsdf_graph_set_events": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
         "tsdf_get_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
@@ -266,6 +267,17 @@ def _dev_ptr(t, n: int, what: str) -> int:
     if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
         raise ValueError(f"{what} must be a contiguous float32 tensor of {n} elements")
     return t.data_ptr()
+
+
+def _host_ptr(a, n: int, what: str) -> int:
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{what} must be a contiguous float32 CPU tensor of {n} elements")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"{what} must be a contiguous float32 array of {n} elements")
+    return a.ctypes.data
 
 
 def _stream(stream) -> int:
@@ -577,6 +589,20 @@ class Graph:
         _check(self.lib.tsdf_graph_launch(self.h, dptr, vptr, poses.ctypes.data_as(_PD), _dev_ptr(d, n, "depth_out"),
                                           _dev_ptr(nm, 3 * n, "normal_out"), _dev_ptr(vm, 3 * n, "vertex_out"),
                                           _stream(stream)), "tsdf_graph_launch")
+        return out
+
+    def launch_host(self, depths, poses, out, stream=None):
+        """The same step from K host depth maps (torch CPU tensors, pinned for an
+        overlapped copy, or numpy arrays; float32, contiguous). The library
+        copies them on its own stream; keep them unchanged until the step's
+        work on ``stream`` has completed."""
+        n = self.intr.width * self.intr.height
+        hptr = (_P * self.K)(*[_host_ptr(d, n, "depth") for d in depths])
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(self.K, 16))
+        d, nm, vm = out
+        _check(self.lib.tsdf_graph_launch_host(self.h, hptr, poses.ctypes.data_as(_PD), _dev_ptr(d, n, "depth_out"),
+                                               _dev_ptr(nm, 3 * n, "normal_out"), _dev_ptr(vm, 3 * n, "vertex_out"),
+                                               _stream(stream)), "tsdf_graph_launch_host")
         return out
 
     def set_events(self, events):

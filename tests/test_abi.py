@@ -105,6 +105,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.tsdf_evict(None, c3, c3, 0, None, None, None, ctypes.byref(n), None) == tsdf.ERR_INVALID_ARG
     assert lib.tsdf_shift(None, c3, 0, None, None, None, ctypes.byref(n), None) == tsdf.ERR_INVALID_ARG
     assert lib.tsdf_import(None, 1, None, None, None, None) == tsdf.ERR_INVALID_ARG
+    assert lib.tsdf_graph_launch_host(None, None, pose, None, None, None, None) == tsdf.ERR_INVALID_ARG
     lib.tsdf_destroy(None)
 
 

@@ -71,3 +71,49 @@ def test_graph_rejects_bad_arguments():
     for K in (0, 9):
         with pytest.raises(tsdf.TsdfError):
             tsdf.Graph(vol, seq.intr, K)
+
+
+@pytest.mark.parametrize("K,pinned", [(1, True), (1, False), (4, True)], ids=["K1-pinned", "K1-pageable", "K4-pinned"])
+def test_host_input_steps_equal_device_input_steps(K, pinned):
+    """tsdf_graph_launch_host: the library's copy (private stream, two staging
+    sets used alternately) gives the same volume and maps bit for bit as steps
+    fed from device maps; steps are enqueued back to back, so a staging set is
+    reused while earlier steps may still run."""
+    seq = synth.sphere_sequence(n_frames=12)
+    H, W = seq.intr.height, seq.intr.width
+    d = [torch.from_numpy(x).cuda() for x in seq.depth]
+    host = torch.from_numpy(seq.depth)
+    host = host.pin_memory() if pinned else seq.depth
+    dev_vol = tsdf.Volume.from_params(seq.volume)
+    host_vol = tsdf.Volume.from_params(seq.volume)
+    gd, gh = tsdf.Graph(dev_vol, seq.intr, K), tsdf.Graph(host_vol, seq.intr, K)
+    ref_maps, got_maps = [], []
+    for k0 in range(0, seq.n_frames, K):
+        ref_maps.append(gd.launch(d[k0:k0 + K], seq.poses[k0:k0 + K], _maps(H, W)))
+        got_maps.append(gh.launch_host([host[k] for k in range(k0, k0 + K)], seq.poses[k0:k0 + K], _maps(H, W)))
+    torch.cuda.synchronize()
+    for a, b in zip(ref_maps, got_maps):
+        _same_maps(a, b)
+    assert gh.instantiations == 1
+    host_vol.check()
+    _same_volume(dev_vol, host_vol)
+    assert host_vol.stats()["frames"] == seq.n_frames
+    gd.close()
+    gh.close()
+
+
+def test_host_input_rejects_bad_arguments():
+    seq = synth.sphere_sequence(n_frames=1)
+    vol = tsdf.Volume.from_params(seq.volume)
+    g = tsdf.Graph(vol, seq.intr, 1)
+    H, W = seq.intr.height, seq.intr.width
+    with pytest.raises(ValueError):            # wrong size
+        g.launch_host([np.zeros((H, W + 1), np.float32)], [seq.poses[0]], _maps(H, W))
+    with pytest.raises(ValueError):            # a device tensor where a host map belongs
+        g.launch_host([torch.zeros((H, W), device="cuda")], [seq.poses[0]], _maps(H, W))
+    bad = np.array(seq.poses[0], dtype=np.float64).copy()
+    bad[0, 3] = np.nan
+    with pytest.raises(tsdf.TsdfError):
+        g.launch_host([seq.depth[0]], [bad], _maps(H, W))
+    assert vol.stats()["frames"] == 0
+    g.close()
