@@ -220,3 +220,61 @@ def test_room_fullsize_sampled_voxels():
                                seq.volume.truncation)
     assert v["ok"], v
     assert v["compared"] > 300, v
+
+
+def test_room_fullsize_sampled_raycast():
+    """Full-size room (640x480, 2048^3 grid of 1.5 mm voxels) in the benchmark's
+    launch configuration: one CUDA graph per frame, the persistent raycast and
+    the integrate shape it times. After 8 frames the raycast maps at 2500
+    sampled pixels meet the bars of compare_raycast against the oracle's march
+    over its own fused field; each sampled pixel's silhouette and
+    multiple-crossing status comes from the oracle's 5x5 neighbourhood of it."""
+    from paper_1311_7194_b300.pipeline import FusionPipeline
+    seq = synth.room_sequence(n_frames=8, device="cuda")
+    vol = tsdf.Volume.from_params(seq.volume)
+    vol.set_launch_config(raycast_persistent=1, integrate_voxels_per_thread=4, integrate_ctas_per_sm=16)
+    pipe = FusionPipeline(vol, seq.intr, graph=True)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, amb_px=AMB_PX)
+    for k in range(seq.n_frames):
+        pipe.step(_cuda(seq.depth[k]), seq.poses[k])
+        ov.fuse(seq.depth[k], seq.poses[k])
+    vol.check()
+    gd, gn, gv = (t.cpu().numpy() for t in pipe.maps)
+    pose = seq.poses[-1]
+    H, W = seq.intr.height, seq.intr.width
+    s, delta = seq.volume.voxel_size, seq.volume.truncation
+    rng = np.random.default_rng(11)
+    n = 2500
+    cu, cv = rng.integers(2, W - 2, n), rng.integers(2, H - 2, n)
+    dy, dx = np.meshgrid(np.arange(-2, 3), np.arange(-2, 3), indexing="ij")
+    pu, pv = cu[:, None, None] + dx, cv[:, None, None] + dy          # (n, 5, 5) patches
+    od, ovx, onr, ofl = ov.raycast(pose, uv=np.stack([pu.ravel(), pv.ravel()], -1))
+    od, ovx, onr, ofl = od.reshape(n, 5, 5), ovx.reshape(n, 5, 5, 3), onr.reshape(n, 5, 5, 3), ofl.reshape(n, 5, 5)
+    dirs = compare.ray_dirs(seq.intr, pose)
+    sil = np.array([compare.silhouette(od[i], (ofl[i] & 1) > 0, onr[i], ofl[i], dirs[pv[i], pu[i]], delta)[2, 2]
+                    for i in range(n)])
+    o_hit, multi = (ofl[:, 2, 2] & 1) > 0, (ofl[:, 2, 2] & 8) > 0
+    o_d, o_v, o_n = od[:, 2, 2], ovx[:, 2, 2], onr[:, 2, 2]
+    g_d, g_v, g_n = gd[cv, cu], gv[cv, cu], gn[cv, cu]
+    g_hit = g_d > 0
+    clear = ~sil & ~multi
+    assert not np.any(clear & (g_hit != o_hit)), "hit / miss differs away from silhouettes"
+    both = clear & g_hit & o_hit
+    assert both.sum() >= 300, int(both.sum())
+    dz = np.abs(g_d[both] - o_d[both]) / s
+    dv = np.linalg.norm(g_v[both] - o_v[both], axis=-1) / s
+    cosang = np.clip((g_n[both] * o_n[both]).sum(-1), -1.0, 1.0)
+    assert dz.max() <= 0.1, float(dz.max())
+    assert dv.max() <= 0.2, float(dv.max())
+    assert np.degrees(np.arccos(cosang)).max() <= 5.0
+    # several crossings within a coarse step: a GPU hit must be a zero of the
+    # oracle's field, not nearer than the oracle's first crossing
+    amb = ~sil & multi & g_hit
+    if amb.any():
+        dc = np.stack([(cu[amb] - seq.intr.cx) / seq.intr.fx, (cv[amb] - seq.intr.cy) / seq.intr.fy,
+                       np.ones(int(amb.sum()))], -1)
+        P = np.asarray(pose)
+        pts = P[:3, 3] + (g_d[amb][:, None] * dc) @ P[:3, :3].T
+        f = ov.field(pts) / s
+        assert np.all(np.abs(f) <= 0.02), float(np.nanmax(np.abs(f)))
+        assert np.all(~o_hit[amb] | (g_d[amb] >= o_d[amb] - 0.1 * s))
