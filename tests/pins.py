@@ -966,12 +966,15 @@ ICP_PINS = [pin_icp_recovers_a_known_motion, pin_icp_scaled_equals_unscaled,
 MESH_PINS = [pin_mesh_sphere_closed_and_outward, pin_mesh_every_case_closed]
 
 
-def run_all(lib_path=None) -> list:
-    """Names of the pins that fail for the library at ``lib_path``."""
+def run_all(lib_path=None, stop_at_first: bool = False) -> list:
+    """Names of the pins that fail for the library at ``lib_path`` (only the
+    first one with ``stop_at_first``)."""
     failed = []
     for pin in ALL_PINS:
         try:
             pin(lib_path)
         except AssertionError:
             failed.append(pin.__name__)
+            if stop_at_first:
+                break
     return failed

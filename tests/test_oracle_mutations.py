@@ -91,12 +91,36 @@ def variants(tmp_path_factory):
         return {k: v.result() for k, v in jobs.items()}
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(variants, name):
+def _run_pins(lib_path):
+    """The pins against one variant, in a process of its own (a planted mistake
+    may crash the oracle); stops at the first pin that fails."""
     code = ("import sys, json; sys.path.insert(0, %r); sys.path.insert(0, %r); import pins; "
-            "print(json.dumps(pins.run_all(%r)))" % (ROOT, os.path.join(ROOT, "tests"), variants[name]))
-    env = dict(os.environ, OMP_NUM_THREADS=str(min(8, os.cpu_count() or 1)))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+            "print(json.dumps(pins.run_all(%r, stop_at_first=True)))" % (ROOT, os.path.join(ROOT, "tests"), lib_path))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+
+
+@pytest.fixture(scope="module")
+def outcomes(variants):
+    """Every variant's pin run, and one of the unmodified oracle, the processes
+    side by side."""
+    runs = dict(variants, unmodified=oracle.build())
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        jobs = {name: ex.submit(_run_pins, path) for name, path in runs.items()}
+        return {k: v.result() for k, v in jobs.items()}
+
+
+def test_unmodified_oracle_passes_the_same_run(outcomes):
+    """The harness itself: the oracle as committed, run the same way, exits
+    cleanly with no failing pin (so a crash below means the planted mistake)."""
+    r = outcomes["unmodified"]
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert json.loads(r.stdout.strip().splitlines()[-1]) == []
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(outcomes, name):
+    r = outcomes[name]
     if r.returncode != 0:
         return      # the planted mistake crashed the oracle: caught
     failed = json.loads(r.stdout.strip().splitlines()[-1])
