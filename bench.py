@@ -408,6 +408,9 @@ def run_ours(args):
                                        "same steps with CUDA event nodes at every stage boundary"},
             "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,
             "rays_per_s": rays_per_step * args.steps * world / elapsed_max,
+            # the same counts over their own stage's time (stage-timing pass)
+            "voxel_updates_per_s_integrate_stage": updates_per_step / (stage_ms_per_step[1] / 1000.0),
+            "rays_per_s_raycast_stage": rays_per_step / (stage_ms_per_step[2] / 1000.0),
             "stage_ms_per_step": {"allocate": stage_ms_per_step[0], "integrate": stage_ms_per_step[1],
                                   "raycast": stage_ms_per_step[2]},
             "work_per_step": {"voxel_updates": int(updates_per_step), "blocks": int(st["n_blocks"]),
