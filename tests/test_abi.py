@@ -127,3 +127,19 @@ def test_binding_refuses_cpu_tensors(lib):
     import torch
     with pytest.raises((TypeError, RuntimeError)):
         tsdf._dev_ptr(torch.zeros(4), 4, "depth")
+
+
+def test_host_map_argument_checks():
+    """The binding's host-map marshalling (tsdf_graph_launch_host): contiguous
+    float32 host arrays of the image size pass as their own address; anything
+    else is refused before the library is called."""
+    import numpy as np
+    import torch
+    a = np.zeros((4, 6), np.float32)
+    assert tsdf._host_ptr(a, 24, "depth") == a.ctypes.data
+    t = torch.zeros((4, 6), dtype=torch.float32)
+    assert tsdf._host_ptr(t, 24, "depth") == t.data_ptr()
+    for bad in (np.zeros((4, 6), np.float64), np.zeros((4, 7), np.float32), np.zeros((6, 4), np.float32).T,
+                torch.zeros((4, 6), dtype=torch.float64), [0.0] * 24):
+        with pytest.raises(ValueError):
+            tsdf._host_ptr(bad, 24, "depth")
