@@ -305,9 +305,11 @@ class OracleVolume:
 
 
 def replay_voxels(vol, intr, depths: Seq[np.ndarray], poses: np.ndarray, voxels: np.ndarray,
-                  alloc_frame: np.ndarray, vars_: Optional[Seq[np.ndarray]] = None, **kw):
-    """Per-voxel Alg. 3 replay over a sequence (sampled full-size parity)."""
-    L = lib()
+                  alloc_frame: np.ndarray, vars_: Optional[Seq[np.ndarray]] = None,
+                  lib_path: Optional[str] = None, **kw):
+    """Per-voxel Alg. 3 replay over a sequence (sampled full-size parity): each
+    listed voxel takes every frame from its block's allocation frame on."""
+    L = lib(lib_path)
     p = make_params(vol, **kw)
     it = make_intr(intr)
     ds = [_f32(d) for d in depths]

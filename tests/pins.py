@@ -948,6 +948,129 @@ def pin_fusing_into_a_shifted_volume_matches_the_unshifted_one(lib_path=None):
     assert np.max(np.abs(Pa[both] - Pb[both]) / Pa[both]) < 1e-9
 
 
+# ----------------------------------------------------------------------------
+# per-voxel replay (the sampled full-size parity checker) and the raycast's
+# crossing-uniqueness flag
+# ----------------------------------------------------------------------------
+
+def pin_replay_closed_form(lib_path=None):
+    """The per-voxel replay of a sequence applies Alg. 3 to the frames from the
+    voxel's allocation frame on. With Q = 0 and a static camera seeing a
+    fronto-parallel plane at depth D_k in frame k (T_k = D_k - z exactly), the
+    result is the inverse-variance weighted mean over exactly those frames
+    f >= a whose |T_k| <= delta: T = sum(T_k/p_k)/sum(1/p_k), P = 1/sum(1/p_k).
+    Allocation frames are drawn at random per voxel (including before the first
+    frame and after the last), so a replay that starts a frame early or late,
+    or ignores the allocation frame, disagrees with the closed form."""
+    vol = _plane_volume()
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    n = 9
+    D, p, depths, vars_ = _const_frames(n, seed=21, spread=4e-3)
+    rng = np.random.default_rng(22)
+    G = vol.grid_dim
+    s = float(np.float32(vol.voxel_size))
+    # voxels whose camera depth lies within 1.5 delta of the plane's depths
+    iz_lo = int((0.5 - 1.5 * vol.truncation - vol.origin[2]) / s)
+    iz_hi = int((0.5 + 1.5 * vol.truncation - vol.origin[2]) / s)
+    m = 6000
+    vox = np.stack([rng.integers(0, G, m), rng.integers(0, G, m), rng.integers(iz_lo, iz_hi + 1, m)], -1)
+    alloc = rng.integers(-1, n + 1, m).astype(np.int32)
+    T, P, amb = oracle.replay_voxels(vol, intr, depths, np.stack([np.eye(4)] * n), vox, alloc, vars_,
+                                     lib_path=lib_path)
+    Tk = D[None, :] - _voxel_world(vol, vox)[:, 2:3]          # (voxels, frames)
+    delta = vol.truncation
+    frames = np.arange(n)[None, :] >= alloc[:, None]
+    valid = (np.abs(Tk) < delta * (1 - 1e-6)) & frames
+    clear = ((np.abs(Tk) < delta * (1 - 1e-6)) | (np.abs(Tk) > delta * (1 + 1e-6))).all(1)
+    w = np.where(valid, 1.0 / p[None, :], 0.0)
+    some = valid.any(1) & clear
+    late = some & (alloc > 0) & (alloc < n)
+    assert some.sum() > 2000 and late.sum() > 1500, (some.sum(), late.sum())
+    assert not amb[clear].any()
+    T_exp = (Tk[some] * w[some]).sum(1) / w[some].sum(1)
+    assert np.allclose(T[some], T_exp, rtol=0, atol=1e-12), np.abs(T[some] - T_exp).max()
+    assert np.allclose(P[some], 1.0 / w[some].sum(1), rtol=1e-12, atol=0)
+    none = ~valid.any(1) & clear
+    assert none.sum() > 200 and np.isnan(T[none]).all() and np.isnan(P[none]).all()
+
+
+def pin_replay_equals_integrate(lib_path=None):
+    """Replaying every voxel of every allocated block from its block's
+    allocation frame reproduces the sparse volume that allocation plus Alg. 3
+    integration built frame by frame, bit for bit (the same measurement and
+    update in the same order per voxel), including blocks that joined the pool
+    mid-sequence. The full-size voxel parity rests on this equivalence."""
+    seq = synth.sphere_sequence(n_frames=6)
+    ov = oracle.OracleVolume(seq.volume, seq.intr, lib_path=lib_path)
+    _fuse(ov, seq.depth, seq.poses)
+    e = ov.export()
+    assert (e.alloc_frame > 0).sum() > 50, (e.alloc_frame > 0).sum()
+    vox = oracle.voxel_coords(e)
+    T, P, amb = oracle.replay_voxels(seq.volume, seq.intr, list(seq.depth), seq.poses, vox,
+                                     np.repeat(e.alloc_frame, 512), lib_path=lib_path)
+    Te, Pe = e.T.ravel(), e.P.ravel()
+    assert np.array_equal(T, Te, equal_nan=True)
+    assert np.array_equal(P, Pe, equal_nan=True)
+    assert np.array_equal(amb, e.amb.ravel())
+    assert (~np.isnan(Te)).sum() > 100000
+
+
+def _slab_volume(thick, lib_path=None, cut=None):
+    """Blocks holding the lattice samples of an analytic field of the world z
+    alone, imported straight into an oracle volume: a single plane at z_front
+    (T = z_front - z, positive on the camera side) when thick is None, else a
+    slab from z_front to z_back = z_front + thick * delta
+    (T = max(z_front - z, z - z_back)); chi where |T| > delta, and behind
+    z_front + cut * delta when cut is given. z_front lies a
+    quarter voxel past a lattice plane. Along z the trilinear field is the
+    linear interpolation of those samples, whose zero crossings are exactly
+    z_front and z_back (both ends of each crossing's lattice interval lie on
+    the same face's branch). Returns (volume, z_front)."""
+    vol = _plane_volume(G=64, z_centre=0.5)
+    intr = synth.Intrinsics.centred(30.0, 32, 24)
+    s = float(np.float32(vol.voxel_size))
+    delta = float(np.float32(vol.truncation))
+    o = vol.origin[2]
+    z_front = o + (round((0.5 - o) / s) + 0.25) * s
+    nb = vol.grid_dim // 8
+    bz, by, bx = np.meshgrid(np.arange(nb), np.arange(nb), np.arange(nb), indexing="ij")
+    coords = np.stack([bx.ravel(), by.ravel(), bz.ravel()], -1)
+    l = np.arange(512)
+    z = o + (coords[:, 2:3] * 8 + (l >> 6)[None, :]) * s
+    T = z_front - z if thick is None else np.maximum(z_front - z, z - (z_front + thick * delta))
+    T = np.where(np.abs(T) <= delta, T, np.nan)
+    if cut is not None:
+        T = np.where(z <= z_front + cut * delta, T, np.nan)
+    keep = ~np.isnan(T).all(1)
+    ov = oracle.OracleVolume(vol, intr, lib_path=lib_path)
+    ov.import_blocks(coords[keep], T[keep], np.ones_like(T[keep]))
+    return ov, z_front
+
+
+def pin_crossing_uniqueness(lib_path=None):
+    """The raycast flags a hit (flag 8) when the field along its ray changes
+    sign more than once, or is undefined, within a coarse step (delta/2) of the
+    crossing: a march that samples every delta/2 could then return another zero
+    crossing. Analytic fields fix the answer:
+      * a single plane has one crossing on every ray: no hit is flagged;
+      * a slab 0.3 delta thick puts a second crossing 0.3 delta behind the
+        first: every hit is flagged;
+      * a slab 0.8 delta thick puts it beyond delta/2: no hit is flagged;
+      * a plane whose field is chi from 0.2 delta behind it on has undefined
+        samples within delta/2 of the crossing: every hit is flagged.
+    In each case the hit depth is the front face."""
+    pose = np.eye(4)
+    pose[:3, 3] = [0.001, -0.002, 0.0]
+    for thick, cut, flagged in [(None, None, False), (0.3, None, True), (0.8, None, False), (None, 0.2, True)]:
+        ov, z_front = _slab_volume(thick, lib_path, cut)
+        depth, _, _, flags = ov.raycast(pose)
+        hit = (flags & 1) > 0
+        assert hit.sum() > 30, hit.sum()
+        assert np.allclose(depth[hit], z_front, rtol=0, atol=1e-9), np.abs(depth[hit] - z_front).max()
+        f8 = (flags[hit] & 8) > 0
+        assert f8.all() if flagged else not f8.any(), (thick, f8.mean())
+
+
 ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_state,
             pin_alg1_running_average, pin_alg2_weighted_average,
             pin_first_measurement_and_quadratic_variance, pin_projection_nearest_pixel,
@@ -957,7 +1080,8 @@ ALL_PINS = [pin_kalman_closed_form, pin_eq9_mean, pin_process_variance_steady_st
             pin_refined_tk_plane_distances, pin_refined_tk_sphere_distance,
             pin_evict_takes_the_blocks_outside_the_box_and_import_restores,
             pin_import_refuses_duplicates_and_allocated_blocks, pin_shift_and_its_inverse_restore_the_volume,
-            pin_fusing_into_a_shifted_volume_matches_the_unshifted_one]
+            pin_fusing_into_a_shifted_volume_matches_the_unshifted_one, pin_replay_closed_form,
+            pin_replay_equals_integrate, pin_crossing_uniqueness]
 
 # the registration oracle is numpy code (oracle/icp.py); its own mutation test
 # plants mistakes in copies of that module

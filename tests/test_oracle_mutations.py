@@ -1,7 +1,7 @@
 """Plant plausible mistakes in copies of the oracle and check that the pins catch
 each one: evidence that the pins constrain every part of the oracle.
 
-Each mutation is a textual edit of ``oracle/tsdf_oracle.cpp`` compiled into a
+Each mutation is a textual edit of ```oracle/tsdf_oracle.cpp`` compiled into a
 temporary library; the pins run against it in a child process (so a mutation that
 crashed would fail the child, not this test run). The real oracle is untouched.
 """
@@ -76,6 +76,13 @@ MUTATIONS = [
      "if (b.b[r] < lo[r] || b.b[r] > hi[r]) return true;"),
     ("import_drops_values", "blk.chi[l] = 0;\n                blk.T[l] = t;", "blk.chi[l] = 0;\n                blk.T[l] = 0.0;"),
     ("import_allows_allocated", "if (v.index.count(keys.back())) return -1;", "(void)0;"),
+    ("replay_one_frame_late", "fi = std::max(0, alloc_frame[k]);", "fi = std::max(0, alloc_frame[k] + 1);"),
+    ("replay_ignores_allocation_frame", "fi = std::max(0, alloc_frame[k]);", "fi = 0;"),
+    ("crossing_two_changes_unique", "return changes <= 1;", "return changes <= 2;"),
+    ("crossing_always_unique", "return changes <= 1;", "return true;"),
+    ("crossing_window_doubled", "const double h = 0.5 * (double)v.p.truncation;",
+     "const double h = (double)v.p.truncation;"),
+    ("crossing_skips_undefined", "if (!trilinear(v, p, &f)) return false;", "if (!trilinear(v, p, &f)) continue;"),
 ]
 
 
