@@ -16,8 +16,8 @@ the last raycast maps read back every step.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the CPU oracle (plain FP64 C++, all host cores) on a
-bounded sample of the same workload and prints the same JSON line with
-"impl": "reference".
+bounded sample of the same workload (each step: one whole frame fused and
+raycast, all timed) and prints the same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -65,8 +65,7 @@ def parse():
                          "1000 frames fused K=8 per graph launch, raycast per batch; capsules: 1280x1024 "
                          "small objects on a 4096^3 grid of 0.15 mm voxels; sphere: the 160x120 parity scene; "
                          "tracking: raycast -> ICP -> fuse at the registered pose; mesh: marching-cubes extraction")
-    ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: frames fused")
-    ap.add_argument("--cpu-ray-stride", type=int, default=8, help="oracle sample: pixel stride per axis")
+    ap.add_argument("--cpu-frames", type=int, default=3, help="oracle sample: whole frames fused and raycast")
     return ap.parse_args()
 
 
@@ -148,29 +147,26 @@ class ClockSampler:
 # CPU oracle sample (the reported CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(seq, frames, stride, ov=None, start=0):
-    """Time the oracle fusing ``frames`` frames (allocate + Alg. 3 over every
-    allocated block) and raycasting every ``stride``-th pixel per axis; returns
-    (seconds per full frame, the oracle volume)."""
-    import numpy as np
+def oracle_sample(seq, frames, ov=None, start=0):
+    """Time the oracle on ``frames`` whole frames of the sequence from ``start``:
+    each fuses the frame (allocate + Alg. 3 over every allocated block) and
+    raycasts every pixel at the frame's pose, as one step of the GPU path does.
+    Nothing is extrapolated: returns (measured seconds per frame, seconds of
+    fusion, seconds of raycasting, the oracle volume)."""
     import oracle
     if ov is None:
         ov = oracle.OracleVolume(seq.volume, seq.intr)
     t_fuse = t_ray = 0.0
-    H, W = seq.intr.height, seq.intr.width
-    vv, uu = np.meshgrid(np.arange(0, H, stride), np.arange(0, W, stride), indexing="ij")
-    uv = np.stack([uu.ravel(), vv.ravel()], -1)
-    scale = (H * W) / uv.shape[0]
     for k in range(start, start + frames):
         f = k % seq.n_frames
         t0 = time.perf_counter()
         ov.fuse(seq.depth[f], seq.poses[f])
         t1 = time.perf_counter()
-        ov.raycast(seq.poses[f], uv)
+        ov.raycast(seq.poses[f])
         t2 = time.perf_counter()
         t_fuse += t1 - t0
-        t_ray += (t2 - t1) * scale
-    return (t_fuse + t_ray) / frames, ov
+        t_ray += t2 - t1
+    return (t_fuse + t_ray) / frames, t_fuse, t_ray, ov
 
 
 def make_sequence(n_frames, device, block_capacity=None, workload="room"):
@@ -179,6 +175,17 @@ def make_sequence(n_frames, device, block_capacity=None, workload="room"):
         return synth.room_sequence(seed=1, n_frames=n_frames, device=device, grid_dim=3000, voxel_size=1e-3,
                                    block_capacity=block_capacity or (1 << 21), origin=(0.0, -0.036, 0.0))
     return synth.room_sequence(seed=1, n_frames=n_frames, device=device, block_capacity=block_capacity or (1 << 20))
+
+
+def room_config(seq, world, n_frames):
+    """The workload's config, identical in both arms (the GPU launch details go
+    to the line's "launch" key)."""
+    H, W = seq.intr.height, seq.intr.width
+    return {"workload": WORKLOAD, "width": W, "height": H, "grid_dim": int(seq.volume.grid_dim),
+            "voxel_size_m": float(seq.volume.voxel_size), "truncation_m": float(seq.volume.truncation),
+            "block_capacity": int(seq.volume.block_capacity), "sequence_frames": n_frames,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step"}
 
 
 def run_reference(args):
@@ -192,24 +199,29 @@ def run_reference(args):
     ov = None
     k = 0
     for _ in range(args.warmup):
-        _, ov = oracle_sample(seq, frames_per_step, args.cpu_ray_stride, ov, start=k)
+        *_, ov = oracle_sample(seq, frames_per_step, ov, start=k)
         k += frames_per_step
-    per = []
+    per, fuse, ray = [], 0.0, 0.0
     for _ in range(args.steps):
-        t, ov = oracle_sample(seq, frames_per_step, args.cpu_ray_stride, ov, start=k)
+        t, tf, tr, ov = oracle_sample(seq, frames_per_step, ov, start=k)
         k += frames_per_step
         per.append(t)
+        fuse += tf
+        ray += tr
     sec = sum(per) / len(per)
     value = 1.0 / sec
     cores = oracle.num_threads()
-    sample = (f"each step: oracle fuses 1 full 640x480 frame (allocate + Alg. 3 over every allocated "
-              f"block, FP64) and raycasts every {args.cpu_ray_stride}th pixel per axis, scaled to the full "
-              f"frame; frames {args.warmup}..{k - 1} of the sequence after {args.warmup} warm-up frames")
+    H, W = seq.intr.height, seq.intr.width
+    sample = (f"each step: the oracle fuses one whole {W}x{H} frame (allocate + Alg. 3 over every allocated "
+              f"block, FP64) and raycasts every pixel at its pose, all timed; frames {args.warmup}..{k - 1} of "
+              f"the sequence after {args.warmup} warm-up frames")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "config": room_config(seq, world, args.frames), "frames_per_step": frames_per_step,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "fuse_s_per_frame": fuse / args.steps, "raycast_s_per_frame": ray / args.steps,
+                             "rays_per_s": H * W * args.steps / ray},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -398,12 +410,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: seeded analytic room scene, quadratic depth noise, edge dropout",
-            "config": {"workload": WORKLOAD, "frames_per_step": F, "width": W, "height": H, "grid_dim": 2048,
-                       "voxel_size_m": 1.5e-3, "block_capacity": int(seq.volume.block_capacity),
-                       "launch": "one CUDA graph per frame" if args.mode == "graph" else "one C-ABI call per stage",
-                       "launch_shape": tuned or vol.launch_config(),
-                       "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2: 368 MB of depth maps and a 4 GB block pool per step",
+            "config": room_config(seq, world, args.frames), "frames_per_step": F,
+            "launch": {"mode": "one CUDA graph per frame" if args.mode == "graph" else "one C-ABI call per stage",
+                       "shape": tuned or vol.launch_config(),
                        "stage_timing": "stage_ms_per_step and the rooflines' durations: a second timed pass of the "
                                        "same steps with CUDA event nodes at every stage boundary"},
             "voxel_updates_per_s": updates_per_step * args.steps * world / elapsed_max,
@@ -449,11 +458,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        sec, _ = oracle_sample(seq, args.cpu_frames, args.cpu_ray_stride)
+        sec, tf, tr, _ = oracle_sample(seq, args.cpu_frames)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                                "sample": f"oracle fuses the first {args.cpu_frames} frames at 640x480 (allocate + "
-                                          f"Alg. 3 over every allocated block, FP64) and raycasts every "
-                                          f"{args.cpu_ray_stride}th pixel per axis, scaled to full frames"}
+                                "sample": f"the oracle fuses the first {args.cpu_frames} whole frames at {W}x{H} "
+                                          f"(allocate + Alg. 3 over every allocated block, FP64) and raycasts every "
+                                          f"pixel of each at its pose; measured, nothing extrapolated",
+                                "fuse_s_per_frame": tf / args.cpu_frames, "raycast_s_per_frame": tr / args.cpu_frames,
+                                "rays_per_s": H * W * args.cpu_frames / tr}
     vol.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
