@@ -26,7 +26,8 @@
  *   - Every compute call is asynchronous on the given stream (a cudaStream_t
  *     passed as void*, NULL = legacy default stream) and does not synchronise.
  *     Argument errors are returned at once; errors found on the device
- *     (pool exhausted) set a sticky flag that tsdf_get_status reports.
+ *     (pool exhausted; in a TSDF_DEBUG build also a failed index check) set a
+ *     sticky flag that tsdf_get_status reports.
  *   - A volume is not thread safe: serialise calls on one volume.
  *   - No call aborts the process or traps the GPU.
  */
@@ -48,7 +49,9 @@ typedef enum {
     TSDF_ERR_HASH_FULL = 3,     /* reserved: the dense block table never fills */
     TSDF_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
     TSDF_ERR_NOT_READY = 5,     /* reserved */
-    TSDF_ERR_OUT_OF_MEMORY = 6  /* device allocation failed (tsdf_create*, host-input staging) */
+    TSDF_ERR_OUT_OF_MEMORY = 6, /* device allocation failed (tsdf_create*, host-input staging) */
+    TSDF_ERR_BOUNDS = 7         /* a device-side index check failed; only a library built with
+                                   TSDF_DEBUG checks (see tsdf_debug_build) */
 } tsdf_status;
 
 /* How T is held in the pool (P is always float32 and all arithmetic float32;
@@ -231,15 +234,16 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const doubl
  * image. Callers that cannot allow that - a real-time loop with a fixed memory
  * budget that must not stall, an application whose own allocator owns device
  * memory, code recording work for later replay - use this call instead: it
- * takes the range maps from a fixed 10 MiB array inside the library (held by
- * every GPU that loads the library until the process exits) and allocates
- * nothing. Limits and rules:
- *   - K->width * K->height must be at most 1280 * 1024, else
- *     TSDF_ERR_INVALID_ARG;
+ * takes the range maps (one near / far pair per 4x4-pixel tile) from a fixed
+ * 640 KiB array inside the library (held by every GPU that loads the library
+ * until the process exits) and allocates nothing. Limits and rules:
+ *   - the image may have at most 81,920 tiles of 4x4 pixels,
+ *     ceil(W/4) * ceil(H/4) <= 81920 (every image up to 1280 x 1024 pixels),
+ *     else TSDF_ERR_INVALID_ARG;
  *   - the current device must be the volume's device, else TSDF_ERR_INVALID_ARG;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture;
+ *     stream capture. The cached address does not survive cudaDeviceReset;
  *   - all calls on a device share the array, which keeps the last call's
  *     contents (each call clears the maps it uses first); calls whose GPU work
  *     overlaps race on it and must be serialised.
@@ -490,6 +494,22 @@ tsdf_status tsdf_mlp_adam(float* w32, uint16_t* wbf16, float* m, float* v, float
  * depth, var_out: device, n float32. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
 tsdf_status tsdf_quadratic_variance(const float* depth, int64_t n, float sigma_coeff,
                                     float* var_out, void* stream);
+
+/* Debug builds (no counterpart in the paper; the stand-in for a device memory
+ * checker). A library built with TSDF_DEBUG checks, on the device, the block
+ * table keys, the pool slots and the visible-list and range-map indices its
+ * kernels use; a failed check skips the access and sets a sticky error that
+ * tsdf_get_status reports as TSDF_ERR_BOUNDS (nothing traps). The in-tree
+ * build writes it as libtsdf_debug.so next to libtsdf.so.
+ * tsdf_debug_build: 1 in such a library, 0 in the release one.
+ * tsdf_debug_check_slot: reads pool slot `slot` of the volume behind the same
+ * check as the raycast's voxel loads, so that the host can make the check
+ * fail (a slot outside [0, block_capacity)) and see TSDF_ERR_BOUNDS reported;
+ * an in-range slot changes nothing. Synchronous. In a release build it
+ * launches nothing and returns TSDF_ERR_NOT_READY. Errors:
+ * TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+int tsdf_debug_build(void);
+tsdf_status tsdf_debug_check_slot(tsdf_volume* vol, int64_t slot, void* stream);
 
 /* Synchronise the volume's last stream and return the first error seen:
  * a sticky device flag (TSDF_ERR_CAPACITY) or a CUDA error. */

@@ -1,9 +1,12 @@
 """Build libtsdf.so (the C-ABI CUDA library) in-tree for sm_103a with nvcc.
 
-    python -m paper_1311_7194_b300.build [--force] [--verbose]
+    python -m paper_1311_7194_b300.build [--force] [--verbose] [--debug]
 
 Objects go to ``paper_1311_7194_b300/_build/``; the shared library is written
-next to this file so that it travels with the source tree.
+next to this file so that it travels with the source tree. ``--debug`` builds
+libtsdf_debug.so instead: the same sources with TSDF_DEBUG defined, whose
+kernels check their table, pool and map indices on the device and report a
+failed check as TSDF_ERR_BOUNDS (objects in ``_build/debug/``).
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtsdf.so")
+LIB_DEBUG = os.path.join(HERE, "libtsdf_debug.so")
 SOURCES = ["tsdf_volume.cu", "tsdf_alloc.cu", "tsdf_integrate.cu", "tsdf_raycast.cu", "tsdf_noalloc.cu", "tsdf_graph.cu",
            "tsdf_autotune.cu", "tsdf_mlp.cu", "tsdf_icp.cu", "tsdf_mesh.cu", "tsdf_evict.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,26 +43,30 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, "tsdf_internal.cuh"), os.path.join(CSRC, "tsdf_storage.cuh"),
+              os.path.join(CSRC, "tsdf_mlp.cuh"),
               os.path.join(INCLUDE, "tsdf.h")]
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
+    obj_dir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
+    flags = NVCC_FLAGS + (["-DTSDF_DEBUG"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -70,11 +78,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, debug="--debug" in sys.argv))

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256) alloc_mark_kernel(const float* __restrict
         }
         const bool fresh = key != kNoKey && key != last;
         if (key != kNoKey) last = key;
-        if (fresh && __ldg(blk_slot + key) < 0) {
+        if (fresh && in_bounds(p.err, (unsigned long long)key < (unsigned long long)p.nb * p.nb * p.nb) &&
+            __ldg(blk_slot + key) < 0) {
             const unsigned bit = 1u << (key & 31u);
             unsigned int* w = newbits + (key >> 5);
             if (!(*(volatile unsigned int*)w & bit)) atomicOr(w, bit);
@@ -154,14 +155,16 @@ __global__ void __launch_bounds__(kTileThreads) alloc_assign_kernel(unsigned int
             bits &= bits - 1u;
             const unsigned key = key0 + 32u * (unsigned)k + b;
             if (rank < cap) {
-                const int bx = (int)(key % (unsigned)nb);
-                const int by = (int)((key / (unsigned)nb) % (unsigned)nb);
-                const int bz = (int)(key / ((unsigned)nb * (unsigned)nb));
-                blk_slot[key] = (int)rank;
-                blocks[rank] = make_int4(bx, by, bz, frame);
-                // coarse occupancy used by the raycast to skip empty space
-                const unsigned c2 = (unsigned)(bx / kOcc2) + (unsigned)n2 * ((unsigned)(by / kOcc2) + (unsigned)n2 * (unsigned)(bz / kOcc2));
-                atomicOr(occ2 + (c2 >> 5), 1u << (c2 & 31u));
+                if (in_bounds(&ctr->error, (unsigned long long)key < (unsigned long long)nb * nb * nb)) {
+                    const int bx = (int)(key % (unsigned)nb);
+                    const int by = (int)((key / (unsigned)nb) % (unsigned)nb);
+                    const int bz = (int)(key / ((unsigned)nb * (unsigned)nb));
+                    blk_slot[key] = (int)rank;
+                    blocks[rank] = make_int4(bx, by, bz, frame);
+                    // coarse occupancy used by the raycast to skip empty space
+                    const unsigned c2 = (unsigned)(bx / kOcc2) + (unsigned)n2 * ((unsigned)(by / kOcc2) + (unsigned)n2 * (unsigned)(bz / kOcc2));
+                    atomicOr(occ2 + (c2 >> 5), 1u << (c2 & 31u));
+                }
             } else {
                 over = true;
             }

@@ -33,6 +33,7 @@
 // that frame for the whole block. For a single frame the range rejects few
 // voxels and is not tested.
 #include "tsdf_internal.cuh"
+#include "tsdf_mlp.cuh"
 
 namespace tsdf {
 namespace {
@@ -96,14 +97,21 @@ __device__ __forceinline__ void reset_frame_counters(Counters* ctr) {
 
 // Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
 // the tile has none. Per pixel: meas = (D, p_k), p_k from the variance map when
-// one is given, else the quadratic model (a D^2)^2; D becomes NaN when it is not
-// a valid depth or p_k is not a positive finite variance. One warp per tile, two
-// pixels per lane. Thread 0 also resets the call's counters when `reset` is given.
+// one is given, from the learned-variance network when kLearned (evaluated here,
+// per pixel, with its weights staged in shared memory once per CTA), else the
+// quadratic model (a D^2)^2; D becomes NaN when it is not a valid depth or p_k
+// is not a positive finite variance. One warp per tile, two pixels per lane.
+// Thread 0 also resets the call's counters when `reset` is given.
+template <bool kLearned>
 __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth,
                                                           const float* __restrict__ var, FrameParams p,
                                                           float2* __restrict__ tiles, float2* __restrict__ meas,
-                                                          Counters* __restrict__ reset) {
+                                                          Counters* __restrict__ reset,
+                                                          const __nv_bfloat16* __restrict__ mlp_w) {
     pdl_prologue();
+    __shared__ float smem[kLearned ? kSmemFloats : 1];
+    MlpShared mlp;
+    if (kLearned) mlp = load_weights(mlp_w, smem);
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
     const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
@@ -125,7 +133,9 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restric
                         hi = fmaxf(hi, d);
                     }
                     float pv;
-                    if (var) {
+                    if (kLearned) {
+                        pv = learned_variance(mlp, depth, p, u + k, v);
+                    } else if (var) {
                         pv = __ldg(var + pix);
                     } else {
                         const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
@@ -222,7 +232,8 @@ __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, c
         unsigned base = 0;
         if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-        if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = e;
+        const unsigned at = base + __popc(m & ((1u << lane) - 1u));
+        if (keep && in_bounds(p.err, at < (unsigned)p.cap)) vis[at] = e;
     }
 }
 
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(256) cull_batch_kernel(Counters* __restrict__ 
         unsigned base = 0;
         if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-        if (keep) {
+        if (keep && in_bounds(bp.fp[0].err, base + __popc(m & ((1u << lane) - 1u)) < (unsigned)bp.fp[0].cap)) {
             const size_t i = (size_t)(base + __popc(m & ((1u << lane) - 1u)));
             for (int k = 0; k < bp.K; ++k) {
                 VisibleBlock e;
@@ -408,6 +419,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
     unsigned updates = 0;
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
         const VisibleBlock vb = vis[i];
+        if (!in_bounds(p.err, vb.slot >= 0 && vb.slot < p.cap)) continue;   // uniform over the CTA
         // camera position of this thread's row start (lx = 0)
         const float xr = __fmaf_rn(ly, p.cs[1], __fmaf_rn(lz, p.cs[2], vb.o[0]));
         const float yr = __fmaf_rn(ly, p.cs[4], __fmaf_rn(lz, p.cs[5], vb.o[1]));
@@ -467,6 +479,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
         const VisibleBlock* ve = vis + (size_t)i * kMaxBatch;
         const int slot = ve[0].slot;
+        if (!in_bounds(bp.fp[0].err, slot >= 0 && slot < bp.fp[0].cap)) continue;   // uniform over the CTA
         const int first = blocks[slot].w - bp.f0;     // first batch frame that sees the block
         const size_t off = (size_t)slot * kBlockVoxels + (size_t)v0;
         float tv[4], pv[4];
@@ -573,15 +586,21 @@ void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned gr
 
 }  // namespace
 
+// The measurement map and depth tiles of one frame; with a network set and no
+// variance map, the network gives each pixel's p_k inside the same kernel.
+void launch_depth_tiles(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, float2* tiles,
+                        float2* meas, Counters* reset, cudaStream_t st) {
+    const auto* w = static_cast<const __nv_bfloat16*>(v->mlp_w);
+    if (!var && w)
+        launch_pdl(depth_tiles_kernel<true>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset, w);
+    else
+        launch_pdl(depth_tiles_kernel<false>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
+                   w);
+}
+
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
                              cudaStream_t st) {
-    if (!var && v->mlp_w) {
-        // learned variance: the network's map feeds this frame's update
-        const cudaError_t e = launch_variance_mlp(v, depth, p, v->var_map, st);
-        if (e != cudaSuccess) return e;
-        var = v->var_map;
-    }
-    launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, v->dtiles, v->meas, v->ctr);
+    launch_depth_tiles(v, depth, var, p, v->dtiles, v->meas, v->ctr, st);
     launch_pdl(cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
@@ -594,18 +613,10 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
 
 cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cudaStream_t st) {
     BatchParams bp = bp_in;
-    if (!bp.var[0] && v->mlp_w) {
-        for (int k = 0; k < bp.K; ++k) {
-            float* vk = v->var_batch + k * v->var_batch_stride;
-            const cudaError_t e = launch_variance_mlp(v, bp.depth[k], bp.fp[k], vk, st);
-            if (e != cudaSuccess) return e;
-            bp.var[k] = vk;
-        }
-    }
     for (int k = 0; k < bp.K; ++k) {
         float2* mk = v->meas_batch + k * v->var_batch_stride;
-        launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, bp.depth[k], bp.var[k], bp.fp[k],
-                   v->dtiles_batch + k * v->dtiles_batch_stride, mk, k == 0 ? v->ctr : nullptr);
+        launch_depth_tiles(v, bp.depth[k], bp.var[k], bp.fp[k], v->dtiles_batch + k * v->dtiles_batch_stride, mk,
+                           k == 0 ? v->ctr : nullptr, st);
         bp.meas[k] = mk;
     }
     launch_pdl(cull_batch_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, bp, v->dtiles_batch,

@@ -14,11 +14,18 @@ constexpr int kSide = 8;                 // M: voxels per block axis
 constexpr int kBlockVoxels = 512;        // M^3
 constexpr int kTileWords = 4096;         // new-block bitmap words per scan tile
 constexpr int kTileThreads = 256;        // threads per scan tile (16 words each)
-constexpr unsigned kErrCapacity = 1u;    // sticky device error bits
+constexpr unsigned kErrCapacity = 1u;    // sticky device error bits: pool exhausted
+constexpr unsigned kErrBounds = 2u;      // a device-side index check failed (TSDF_DEBUG builds)
 constexpr int kDepthTile = 8;            // depth min / max tiles used by the integrate cull
 constexpr int kMaxBatch = 8;             // frames per tsdf_integrate_batch call
 constexpr int kMlpParams = 1985;         // learned-variance network: 27-32-32-1
 constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
+constexpr int kRangeTile = 4;            // raycast range maps hold one near / far pair per 4x4 pixels
+
+// Entries of one raycast range map (near or far) for a width x height image.
+inline int64_t range_tiles(int width, int height) {
+    return (int64_t)((width + kRangeTile - 1) / kRangeTile) * ((height + kRangeTile - 1) / kRangeTile);
+}
 
 // Device-resident counters; every data-dependent size lives here so that a
 // sequence of calls needs no host round trip (and can be graph captured).
@@ -65,6 +72,7 @@ struct AllocParams {
     int J;
     int nb;
     int width, height;
+    unsigned int* err;   // the volume's sticky device error word
 };
 
 // Constants of one integrate / raycast call.
@@ -88,6 +96,8 @@ struct FrameParams {
     int width, height;
     int nb, G;
     int n2;              // occupancy cells per axis (cells of 4^3 blocks)
+    int cap;             // pool capacity in blocks (index checks of TSDF_DEBUG builds)
+    unsigned int* err;   // the volume's sticky device error word
 };
 
 // Constants of one batched integrate call: K frames fused in order.
@@ -129,19 +139,17 @@ struct tsdf_volume {
     tsdf::VisibleBlock* visible;   // [cap]
     int* visible_rc;               // [cap]
     tsdf::Counters* ctr;
-    unsigned int* range;           // raycast near / far maps, 2 * range_pixels
-    int64_t range_pixels;
+    unsigned int* range;           // raycast near / far maps (one pair per 4x4 pixels), 2 * range_cap
+    int64_t range_cap;             // entries of each map
     float2* dtiles;                // per 8x8-pixel tile (min, max) of the valid depth
     int64_t dtiles_cap;
     tsdf::VisibleBlock* visible_batch;   // [cap * kMaxBatch] per (block, frame) entries of a batch
     float2* dtiles_batch;          // [kMaxBatch * dtiles_batch_stride]
     int64_t dtiles_batch_stride;
     void* mlp_w;                   // learned-variance weights (bfloat16, device) or null
-    float* var_map;                // variance map made by the network for one frame
     float2* meas;                  // per pixel (depth, or NaN when it gives no measurement; p_k)
-    int64_t var_cap;               // pixels of var_map and meas
-    float* var_batch;              // [kMaxBatch * var_batch_stride]
-    float2* meas_batch;            // [kMaxBatch * var_batch_stride]
+    int64_t var_cap;               // pixels of meas
+    float2* meas_batch;            // [kMaxBatch * var_batch_stride] measurement maps of a batch
     int64_t var_batch_stride;
     double* icp_part;              // registration partial sums (lazily allocated)
     void* mesh_scratch;            // marching cubes: per-block counts and offsets (lazily allocated)
@@ -164,7 +172,7 @@ cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameP
                                 cudaStream_t st);
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
-// Raycast with caller-provided near / far range maps (each W*H words).
+// Raycast with caller-provided near / far range maps (each range_tiles(W, H) words).
 cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intrinsics& K, const double pose[16],
                             const float* mv, const float* mn, const double model_pose[16], const tsdf_icp_params& prm,
                             double* host_sums, float* host_box, cudaStream_t st);
@@ -179,6 +187,9 @@ cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st);
 cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out,
                                       cudaStream_t st);
+// One checked read of a pool slot (tsdf_debug_check_slot); sink: one device float.
+cudaError_t launch_debug_slot(tsdf_volume* v, long long slot, float* sink, cudaStream_t st);
+constexpr double kIdentityPose[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
 
 // Lazily grown per-image buffers and argument checks (tsdf_volume.cu).
 cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st);
@@ -190,6 +201,21 @@ bool intrinsics_valid(const tsdf_intrinsics* K);
 // Host-side constant preparation (tsdf_volume.cu).
 AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);
 FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, const double* pose);
+
+// Index checks of TSDF_DEBUG builds (the stand-in for a memory checker): a
+// check that fails sets kErrBounds in the volume's error word, which
+// tsdf_get_status reports as TSDF_ERR_BOUNDS, and the caller skips the access.
+// Nothing traps. In release builds every check is true and compiles away.
+__device__ __forceinline__ bool in_bounds(unsigned int* err, bool ok) {
+#ifdef TSDF_DEBUG
+    if (!ok) atomicOr(err, kErrBounds);
+    return ok;
+#else
+    (void)err;
+    (void)ok;
+    return true;
+#endif
+}
 
 __device__ __forceinline__ bool depth_ok(float d, float dmin, float dmax) {
     return (fabsf(d) < __int_as_float(0x7f800000)) & (d > 0.0f) & (d >= dmin) & (d <= dmax);

@@ -1,9 +1,9 @@
 // tsdf_raycast_noalloc: the raycast of tsdf_raycast without any device memory
 // allocation during the call.
 //
-// tsdf_raycast keeps its per-pixel near / far range maps in device memory that it
-// grows with cudaMalloc the first time it sees a larger image (and cudaFree of the
-// old maps, which synchronises the device). Some callers cannot have that
+// tsdf_raycast keeps its near / far range maps (one pair per 4x4-pixel tile) in
+// device memory that it grows with cudaMalloc the first time it sees a larger
+// image (and cudaFree of the old maps, which synchronises the device). Some callers cannot have that
 // happen inside the call: a real-time loop whose memory budget is fixed up front
 // and that must not stall on an allocation or on the implicit device-wide
 // synchronisation of cudaFree, an application whose own allocator owns all
@@ -11,58 +11,46 @@
 // entry point takes the range maps from a fixed array that is part of the
 // library's device image instead.
 //
-// The array, tsdf_noalloc_range, holds the maps of one image of at most
-// kNoAllocMaxPixels pixels (1280 x 1024): 2 x 4 bytes per pixel = 10 MiB, held on
-// every GPU that loads the library until the process exits. Larger images are
-// rejected with TSDF_ERR_INVALID_ARG. All calls on a device share the array and
-// it keeps whatever the last call left in it; the kernels clear both maps at the
-// start of every call, so nothing depends on the previous contents. Two calls
-// whose work overlaps on the GPU (different streams, or different volumes on
-// concurrent streams) race on the array and produce garbage: serialise them.
+// The array, tsdf_noalloc_range, holds the near and far range maps of one
+// image: one pair of words per 4x4-pixel tile, at most kNoAllocMaxTiles tiles
+// (81,920: every image of up to 1280 x 1024 pixels), 2 x 4 bytes per tile =
+// 640 KiB, held on every GPU that loads the library until the process exits.
+// Images with more tiles are rejected with TSDF_ERR_INVALID_ARG. All calls on a
+// device share the array and it keeps whatever the last call left in it; the
+// kernels clear both maps at the start of every call, so nothing depends on the
+// previous contents. Two calls whose work overlaps on the GPU (different
+// streams, or different volumes on concurrent streams) race on the array and
+// produce garbage: serialise them.
 //
 // Host code must not use the array's name as a device address (on the host it is
 // only a stand-in symbol). The first call on each device, with that device
 // current, asks the runtime for the array's device address with
 // cudaGetSymbolAddress and caches it; that first call should therefore come
-// before any stream capture on the device.
-#include <cmath>
+// before any stream capture on the device. The cached address belongs to the
+// device's context as it was then: it does not survive cudaDeviceReset.
 #include <mutex>
 
 #include "tsdf_internal.cuh"
 
 namespace {
-constexpr int64_t kNoAllocMaxPixels = 1280 * 1024;
+constexpr int64_t kNoAllocMaxTiles = (1280 / tsdf::kRangeTile) * (1024 / tsdf::kRangeTile);
 constexpr int kMaxDevices = 64;
 }  // namespace
 
-// near map in the first kNoAllocMaxPixels words, far map in the second half
-static __device__ __align__(256) unsigned int tsdf_noalloc_range[2 * kNoAllocMaxPixels];
+// near map in the first kNoAllocMaxTiles words, far map in the second half
+static __device__ __align__(256) unsigned int tsdf_noalloc_range[2 * kNoAllocMaxTiles];
 
 namespace {
 
 std::mutex g_setup_mutex;
 unsigned int* g_range_addr[kMaxDevices];   // device address of tsdf_noalloc_range per device
 
-bool noalloc_pose_ok(const double* pose) {
-    if (!pose) return false;
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(pose[i])) return false;
-    return true;
-}
-
-bool noalloc_intr_ok(const tsdf_intrinsics* K) {
-    if (!K) return false;
-    if (!(std::isfinite(K->fx) && std::isfinite(K->fy) && std::isfinite(K->cx) && std::isfinite(K->cy)))
-        return false;
-    return K->fx != 0.0f && K->fy != 0.0f && K->width > 0 && K->height > 0;
-}
-
 }  // namespace
 
 extern "C" tsdf_status tsdf_raycast_noalloc(tsdf_volume* v, const tsdf_intrinsics* K, const double pose_wc[16],
                                             float* depth_out, float* normal_out, float* vertex_out, void* stream) {
-    if (!v || !noalloc_intr_ok(K) || !noalloc_pose_ok(pose_wc)) return TSDF_ERR_INVALID_ARG;
-    if ((int64_t)K->width * (int64_t)K->height > kNoAllocMaxPixels) return TSDF_ERR_INVALID_ARG;
+    if (!v || !tsdf::intrinsics_valid(K) || !tsdf::pose_valid(pose_wc)) return TSDF_ERR_INVALID_ARG;
+    if (tsdf::range_tiles(K->width, K->height) > kNoAllocMaxTiles) return TSDF_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSDF_ERR_CUDA;
     if (dev != v->device || dev < 0 || dev >= kMaxDevices) return TSDF_ERR_INVALID_ARG;
@@ -83,7 +71,7 @@ extern "C" tsdf_status tsdf_raycast_noalloc(tsdf_volume* v, const tsdf_intrinsic
     const tsdf::FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     cudaStream_t st = (cudaStream_t)stream;
     v->last_stream = st;
-    const cudaError_t e = tsdf::launch_raycast_ranges(v, p, range, range + kNoAllocMaxPixels, depth_out, normal_out,
+    const cudaError_t e = tsdf::launch_raycast_ranges(v, p, range, range + kNoAllocMaxTiles, depth_out, normal_out,
                                                       vertex_out, st);
     if (e != cudaSuccess) {
         if (v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;

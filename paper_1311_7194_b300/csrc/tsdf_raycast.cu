@@ -36,7 +36,6 @@ namespace {
 constexpr int kMaxMarch = 8192;     // bound on march iterations per ray
 constexpr int kRefine = 10;         // refinement samples per hit (Illinois false position)
 constexpr int kFine = 16;           // substeps of the re-scan on entering the field below zero
-constexpr int kRangeTile = 4;       // range maps hold one near / far pair per 4x4 pixels
 constexpr unsigned kFarInit = 0u;   // float bits of +0
 constexpr unsigned kNearInit = 0x7f800000u;   // float bits of +inf
 
@@ -94,7 +93,8 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
         unsigned base = 0;
         if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible_rc, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-        if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = (int)b;
+        const unsigned at = base + __popc(m & ((1u << lane) - 1u));
+        if (keep && in_bounds(p.err, at < (unsigned)p.cap)) vis[at] = (int)b;
     }
 }
 
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const Counters* __restrict_
             const int count = cols * (b1 - b0 + 1);
             for (int k = lane; k < count; k += 32) {
                 const int tile = (b0 + k / cols) * tiles_x + a0 + k % cols;
+                if (!in_bounds(p.err, tile >= 0 && tile < tiles_x * ((p.height + kRangeTile - 1) / kRangeTile))) continue;
                 atomicMin(near_ + tile, zn_j);
                 atomicMax(far_ + tile, zf_j);
             }
@@ -261,6 +262,9 @@ __device__ __forceinline__ int trilinear(const FrameParams& p, const int* __rest
             if (ex & ey & ez) trace_lookup(p, bx + 1, by + 1, bz + 1);
         }
     }
+    // every corner's block is a pool slot below the capacity or unallocated
+    if (!in_bounds(p.err, max(max(max(s000, s100), max(s010, s110)), max(max(s001, s101), max(s011, s111))) < p.cap))
+        return 1;
     const int x0 = lx, x1 = ex ? 0 : lx + 1;
     const int y0 = 8 * ly, y1 = ey ? 0 : 8 * (ly + 1);
     const int z0 = 64 * lz, z1 = ez ? 0 : 64 * (lz + 1);
@@ -842,10 +846,9 @@ void launch_march(tsdf_volume* v, const FrameParams& p, const unsigned int* near
 
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out, float* normal_out,
                            float* vertex_out, cudaStream_t st) {
-    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
-                           ((p.height + kRangeTile - 1) / kRangeTile);
+    const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
-    unsigned int* far_ = v->range + v->range_pixels;
+    unsigned int* far_ = v->range + v->range_cap;
     launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
@@ -880,10 +883,9 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
     const TraceState ts{t_sector, table_sector, counts, storage_bytes(v->cfg.storage)};
     cudaError_t e = cudaMemcpyToSymbolAsync(g_trace, &ts, sizeof(ts), 0, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
-                           ((p.height + kRangeTile - 1) / kRangeTile);
+    const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
-    unsigned int* far_ = v->range + v->range_pixels;
+    unsigned int* far_ = v->range + v->range_cap;
     launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
@@ -897,10 +899,37 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
     return cudaGetLastError();
 }
 
+namespace {
+
+// One read of pool slot `slot` behind the same index check as the raycast's
+// voxel loads (tsdf_debug_check_slot: a check the host can make fail).
+template <int kS>
+__global__ void debug_slot_kernel(const typename Codec<kS>::E* __restrict__ T, long long slot, FrameParams p,
+                                  float* __restrict__ sink) {
+    if (in_bounds(p.err, slot >= 0 && slot < p.cap)) *sink = Codec<kS>::load(T + slot * kBlockVoxels, p.tsc);
+}
+
+}  // namespace
+
+cudaError_t launch_debug_slot(tsdf_volume* v, long long slot, float* sink, cudaStream_t st) {
+    const FrameParams p = make_frame_params(v, tsdf_intrinsics{1.0f, 1.0f, 0.0f, 0.0f, 1, 1}, kIdentityPose);
+    switch (v->cfg.storage) {
+        case TSDF_STORAGE_F16:
+            debug_slot_kernel<TSDF_STORAGE_F16><<<1, 1, 0, st>>>(static_cast<const __half*>(v->T), slot, p, sink);
+            break;
+        case TSDF_STORAGE_SNORM16:
+            debug_slot_kernel<TSDF_STORAGE_SNORM16><<<1, 1, 0, st>>>(static_cast<const short*>(v->T), slot, p, sink);
+            break;
+        default:
+            debug_slot_kernel<TSDF_STORAGE_F32><<<1, 1, 0, st>>>(static_cast<const float*>(v->T), slot, p, sink);
+            break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
                                   float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
-    const long long npix = (long long)((p.width + kRangeTile - 1) / kRangeTile) *
-                           ((p.height + kRangeTile - 1) / kRangeTile);
+    const long long npix = range_tiles(p.width, p.height);
     launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);

@@ -93,9 +93,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->visible_batch);
     cudaFree(v->dtiles_batch);
     cudaFree(v->mlp_w);
-    cudaFree(v->var_map);
     cudaFree(v->meas);
-    cudaFree(v->var_batch);
     cudaFree(v->meas_batch);
     cudaFree(v->icp_part);
     cudaFree(v->mesh_scratch);
@@ -122,6 +120,7 @@ AllocParams make_alloc_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.nb = v->nb;
     p.width = K.width;
     p.height = K.height;
+    p.err = &v->ctr->error;
     return p;
 }
 
@@ -165,6 +164,8 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.nb = v->nb;
     p.G = v->cfg.grid_dim;
     p.n2 = v->n2;
+    p.cap = (int)v->cfg.block_capacity;
+    p.err = &v->ctr->error;
     return p;
 }
 
@@ -184,13 +185,10 @@ cudaError_t ensure_dtiles(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t
         if (e == cudaSuccess) e = cudaMalloc(&v->dtiles, (size_t)ntiles * sizeof(float2));
         if (e == cudaSuccess) v->dtiles_cap = ntiles;
     }
-    if (e == cudaSuccess && npix > v->var_cap) {   // variance map of the learned model, measurement map
-        e = cudaFree(v->var_map);
-        if (e == cudaSuccess) e = cudaFree(v->meas);
-        v->var_map = nullptr;
+    if (e == cudaSuccess && npix > v->var_cap) {   // measurement map
+        e = cudaFree(v->meas);
         v->meas = nullptr;
         v->var_cap = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&v->var_map, (size_t)npix * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v->meas, (size_t)npix * sizeof(float2));
         if (e == cudaSuccess) v->var_cap = npix;
     }
@@ -212,12 +210,9 @@ cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t 
         if (e == cudaSuccess) v->dtiles_batch_stride = ntiles;
     }
     if (e == cudaSuccess && npix > v->var_batch_stride) {
-        e = cudaFree(v->var_batch);
-        if (e == cudaSuccess) e = cudaFree(v->meas_batch);
-        v->var_batch = nullptr;
+        e = cudaFree(v->meas_batch);
         v->meas_batch = nullptr;
         v->var_batch_stride = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&v->var_batch, (size_t)npix * kMaxBatch * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v->meas_batch, (size_t)npix * kMaxBatch * sizeof(float2));
         if (e == cudaSuccess) v->var_batch_stride = npix;
     }
@@ -225,14 +220,14 @@ cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t 
 }
 
 cudaError_t ensure_range(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
-    const int64_t npix = (int64_t)K.width * K.height;
-    if (npix <= v->range_pixels) return cudaSuccess;
+    const int64_t n = range_tiles(K.width, K.height);
+    if (n <= v->range_cap) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaFree(v->range);
     v->range = nullptr;
-    v->range_pixels = 0;
-    if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)npix * sizeof(unsigned int));
-    if (e == cudaSuccess) v->range_pixels = npix;
+    v->range_cap = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)n * sizeof(unsigned int));
+    if (e == cudaSuccess) v->range_cap = n;
     return e;
 }
 
@@ -274,6 +269,7 @@ const char* tsdf_status_string(tsdf_status s) {
         case TSDF_ERR_CUDA: return "CUDA error";
         case TSDF_ERR_NOT_READY: return "not ready";
         case TSDF_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case TSDF_ERR_BOUNDS: return "device index check failed (debug build)";
     }
     return "unknown status";
 }
@@ -590,6 +586,32 @@ tsdf_status tsdf_quadratic_variance(const float* depth, int64_t n, float sigma_c
                : TSDF_ERR_CUDA;
 }
 
+int tsdf_debug_build(void) {
+#ifdef TSDF_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+tsdf_status tsdf_debug_check_slot(tsdf_volume* v, int64_t slot, void* stream) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+#ifdef TSDF_DEBUG
+    cudaStream_t st = (cudaStream_t)stream;
+    float* sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = tsdf::launch_debug_slot(v, (long long)slot, sink, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(sink);
+    v->last_stream = st;
+    return e == cudaSuccess ? TSDF_OK : fail_cuda(v, e);
+#else
+    (void)slot;
+    (void)stream;
+    return TSDF_ERR_NOT_READY;
+#endif
+}
+
 tsdf_status tsdf_get_status(tsdf_volume* v) {
     if (!v) return TSDF_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(v->last_stream);
@@ -598,6 +620,7 @@ tsdf_status tsdf_get_status(tsdf_volume* v) {
     unsigned int err = 0;
     e = cudaMemcpy(&err, &v->ctr->error, sizeof(err), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail_cuda(v, e);
+    if (err & tsdf::kErrBounds) return TSDF_ERR_BOUNDS;
     if (err & tsdf::kErrCapacity) return TSDF_ERR_CAPACITY;
     return TSDF_OK;
 }

@@ -15,13 +15,16 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtsdf.so")
+# the same library built with TSDF_DEBUG: device-side index checks that report
+# TSDF_ERR_BOUNDS (python -m paper_1311_7194_b300.build --debug)
+DEBUG_LIB_PATH = os.path.join(_HERE, "libtsdf_debug.so")
 
-OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_HASH_FULL, ERR_CUDA, ERR_NOT_READY, ERR_OUT_OF_MEMORY = range(7)
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_HASH_FULL, ERR_CUDA, ERR_NOT_READY, ERR_OUT_OF_MEMORY, ERR_BOUNDS = range(8)
 STORAGE_F32, STORAGE_F16, STORAGE_SNORM16 = 0, 1, 2
 UPDATE_KALMAN, UPDATE_AVERAGE, UPDATE_WEIGHTED = 0, 1, 2      # tsdf_update_rule
 
 # Every function the header declares (checked against include/tsdf.h by the tests).
-EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
+EXPORTED = ["tsdf_config_default", "tsdf_status_string", "tsdf_debug_build", "tsdf_debug_check_slot", "tsdf_create", "tsdf_create_ex", "tsdf_destroy",
             "tsdf_reset", "tsdf_allocate", "tsdf_integrate", "tsdf_integrate_batch", "tsdf_raycast",
             "tsdf_raycast_noalloc", "tsdf_raycast_trace", "tsdf_icp_params_default", "tsdf_icp", "tsdf_icp_sums",
             "tsdf_icp_solve", "tsdf_mesh", "tsdf_mesh_case", "tsdf_graph_create", "tsdf_graph_launch", "tsdf_graph_launch_host", "tsdf_graph_instantiations",
@@ -171,6 +174,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tsdf_shift": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, _P, _P, _P,
                                       ctypes.POINTER(ctypes.c_int64), _P]),
         "tsdf_import": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
+        "tsdf_debug_build": (ctypes.c_int, []),
+        "tsdf_debug_check_slot": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,19 +318,19 @@ class Evicted:
 class Volume:
     """A sparse TSDF volume on the current CUDA device (tsdf_create_ex)."""
 
-    def __init__(self, config: Config):
+    def __init__(self, config: Config, lib: Optional[ctypes.CDLL] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtsdf needs a CUDA device")
-        self.lib = load()
+        self.lib = lib or load()
         self.config = config
         h = _P()
         _check(self.lib.tsdf_create_ex(ctypes.byref(config), ctypes.byref(h)), "tsdf_create_ex")
         self.h = h
 
     @classmethod
-    def from_params(cls, vol, **overrides) -> "Volume":
-        return cls(config_from(vol, **overrides))
+    def from_params(cls, vol, lib: Optional[ctypes.CDLL] = None, **overrides) -> "Volume":
+        return cls(config_from(vol, **overrides), lib)
 
     def close(self):
         if getattr(self, "h", None):

@@ -52,9 +52,16 @@ def test_config_defaults(lib):
 
 
 def test_status_strings(lib):
-    for s in range(7):
-        assert lib.tsdf_status_string(s).decode()
+    for s in range(8):
+        assert lib.tsdf_status_string(s).decode() != "unknown status"
     assert lib.tsdf_status_string(99).decode() == "unknown status"
+
+
+def test_release_library_is_not_a_debug_build(lib):
+    """The release library compiles the device index checks out; its
+    tsdf_debug_check_slot launches nothing."""
+    assert lib.tsdf_debug_build() == 0
+    assert lib.tsdf_debug_check_slot(None, 0, None) == tsdf.ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("field,value", [

@@ -64,12 +64,42 @@ def test_noalloc_raycast_matches_raycast_on_two_calls_in_a_row():
         _same(ref, got, seq.volume.voxel_size)
 
 
+def test_noalloc_raycast_after_and_before_a_larger_raycast():
+    """tsdf_raycast on a larger image first grows its own range maps; the
+    no-allocation call at the sequence's image then still matches tsdf_raycast,
+    and a second larger tsdf_raycast after it is bit for bit the first one: the
+    two calls keep their range maps apart."""
+    torch.cuda.set_device(0)
+    lib = tsdf.load()
+    seq = synth.sphere_sequence(n_frames=4)
+    vol = tsdf.Volume.from_params(seq.volume)
+    for k in range(seq.n_frames):
+        vol.fuse(torch.from_numpy(seq.depth[k]).cuda(), seq.intr, seq.poses[k])
+    H, W = seq.intr.height, seq.intr.width
+    big = synth.Intrinsics(2 * seq.intr.fx, 2 * seq.intr.fy, (2 * W - 1) / 2.0, (2 * H - 1) / 2.0, 2 * W, 2 * H)
+    pose = seq.poses[-1]
+    ref = vol.raycast(seq.intr, pose, out=_maps(H, W))
+    big1 = vol.raycast(big, pose, out=_maps(2 * H, 2 * W))
+    got = _maps(H, W)
+    assert _noalloc(lib, vol, seq.intr, pose, got) == tsdf.OK
+    big2 = vol.raycast(big, pose, out=_maps(2 * H, 2 * W))
+    torch.cuda.synchronize()
+    vol.check()
+    _same(ref, got, seq.volume.voxel_size)
+    for a, b in zip(big1, big2):
+        assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0))
+
+
 def test_noalloc_raycast_rejects_images_beyond_its_limit():
+    """The fixed array holds 81,920 range tiles of 4x4 pixels: a 2048 x 1024
+    image and a ragged 1281 x 1021 one (fewer pixels than 1280 x 1024, but
+    321 x 256 tiles) are refused before any GPU work."""
     torch.cuda.set_device(0)
     lib = tsdf.load()
     seq = synth.sphere_sequence(n_frames=1)
     vol = tsdf.Volume.from_params(seq.volume)
-    big = synth.Intrinsics(1400.0, 1400.0, 1023.5, 511.5, 2048, 1024)
     out = _maps(1, 1)
-    assert _noalloc(lib, vol, big, seq.poses[0], out) == tsdf.ERR_INVALID_ARG
+    for W, H in [(2048, 1024), (1281, 1021)]:
+        big = synth.Intrinsics(1400.0, 1400.0, (W - 1) / 2.0, (H - 1) / 2.0, W, H)
+        assert _noalloc(lib, vol, big, seq.poses[0], out) == tsdf.ERR_INVALID_ARG
     vol.check()
