@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "room-scale plain FP32: 640x480, 2048^3 grid of 1.5 mm voxels, 300 frames"
 METRIC, UNIT = "frames/s", "frames/s"
-LAUNCHES_PER_FRAME = 12    # allocate 5 + integrate 3 + raycast 4 kernels
+LAUNCHES_PER_FRAME = 13    # allocate 5 + integrate 3 + raycast 5 kernels (persistent raycast)
 
 
 def parse():
@@ -426,7 +426,7 @@ def run_ours(args):
                               "visible_blocks": int(st["visible_blocks_total"]),
                               "rays_hit": int(st["rays_hit_total"])},
             "roofline": roofline, "roofline_integrate": roofline_integrate,
-            "gpu_launches": LAUNCHES_PER_FRAME * F * args.steps,
+            "gpu_launches": (LAUNCHES_PER_FRAME - (0 if vol.launch_config()["raycast_persistent"] else 1)) * F * args.steps,
             "clocks": clk}
 
     # end to end through the public API with host buffers

@@ -234,12 +234,12 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const tsdf_intrinsics* K, const doubl
  * image. Callers that cannot allow that - a real-time loop with a fixed memory
  * budget that must not stall, an application whose own allocator owns device
  * memory, code recording work for later replay - use this call instead: it
- * takes the range maps (one near / far pair per 4x4-pixel tile) from a fixed
- * 640 KiB array inside the library (held by every GPU that loads the library
- * until the process exits) and allocates nothing. Limits and rules:
- *   - the image may have at most 81,920 tiles of 4x4 pixels,
- *     ceil(W/4) * ceil(H/4) <= 81920 (every image up to 1280 x 1024 pixels),
- *     else TSDF_ERR_INVALID_ARG;
+ * takes its scratch - the range maps (one near / far pair per 4x4-pixel tile)
+ * and the ray-order lists (4 lists of 8x4-pixel tiles) - from a fixed 1.25 MiB
+ * array inside the library (held by every GPU that loads the library until
+ * the process exits) and allocates nothing. Limits and rules:
+ *   - ceil(W/4) * ceil(H/4) <= 81920 and ceil(W/8) * ceil(H/4) <= 40960
+ *     (every image up to 1280 x 1024 pixels), else TSDF_ERR_INVALID_ARG;
  *   - the current device must be the volume's device, else TSDF_ERR_INVALID_ARG;
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any

@@ -27,6 +27,12 @@ inline int64_t range_tiles(int width, int height) {
     return (int64_t)((width + kRangeTile - 1) / kRangeTile) * ((height + kRangeTile - 1) / kRangeTile);
 }
 
+// The persistent raycast hands out rays in 8x4-pixel tiles, the tiles with the
+// longest ranges first: kRayBuckets lists of tile indices, each up to
+// ray_tiles(W, H) entries.
+constexpr int kRayBuckets = 4;
+inline int64_t ray_tiles(int width, int height) { return (int64_t)((width + 7) / 8) * ((height + 3) / 4); }
+
 // Device-resident counters; every data-dependent size lives here so that a
 // sequence of calls needs no host round trip (and can be graph captured).
 struct Counters {
@@ -45,6 +51,7 @@ struct Counters {
     unsigned long long rc_blocks_total;
     unsigned int rc_next;        // next ray handed out by the persistent raycast
     unsigned int pad2;
+    unsigned int rc_bucket[kRayBuckets];   // 8x4-pixel ray tiles per range-length bucket (ray order)
 };
 
 // One visible block for the integrate kernel: pool slot, the camera-space
@@ -141,6 +148,8 @@ struct tsdf_volume {
     tsdf::Counters* ctr;
     unsigned int* range;           // raycast near / far maps (one pair per 4x4 pixels), 2 * range_cap
     int64_t range_cap;             // entries of each map
+    int* ray_order;                // [kRayBuckets * ray_order_cap] ray tiles by range-length bucket
+    int64_t ray_order_cap;
     float2* dtiles;                // per 8x8-pixel tile (min, max) of the valid depth
     int64_t dtiles_cap;
     tsdf::VisibleBlock* visible_batch;   // [cap * kMaxBatch] per (block, frame) entries of a batch
@@ -172,7 +181,8 @@ cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameP
                                 cudaStream_t st);
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
                            float* normal_out, float* vertex_out, cudaStream_t st);
-// Raycast with caller-provided near / far range maps (each range_tiles(W, H) words).
+// Raycast with caller-provided near / far range maps (each range_tiles(W, H)
+// words) and ray-order lists (kRayBuckets * ray_tiles(W, H) words).
 cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intrinsics& K, const double pose[16],
                             const float* mv, const float* mn, const double model_pose[16], const tsdf_icp_params& prm,
                             double* host_sums, float* host_box, cudaStream_t st);
@@ -184,7 +194,7 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
                                  unsigned char* table_sector, long long n_table, unsigned long long* counts,
                                  cudaStream_t st);
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
-                                  float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st);
+                                  int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st);
 cudaError_t launch_quadratic_variance(const float* depth, int64_t n, float a, float* out,
                                       cudaStream_t st);
 // One checked read of a pool slot (tsdf_debug_check_slot); sink: one device float.

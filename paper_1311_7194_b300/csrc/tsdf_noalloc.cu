@@ -12,10 +12,12 @@
 // library's device image instead.
 //
 // The array, tsdf_noalloc_range, holds the near and far range maps of one
-// image: one pair of words per 4x4-pixel tile, at most kNoAllocMaxTiles tiles
-// (81,920: every image of up to 1280 x 1024 pixels), 2 x 4 bytes per tile =
-// 640 KiB, held on every GPU that loads the library until the process exits.
-// Images with more tiles are rejected with TSDF_ERR_INVALID_ARG. All calls on a
+// image (one pair of words per 4x4-pixel tile, at most kNoAllocMaxTiles =
+// 81,920 tiles) and the raycast's ray-order lists (kRayBuckets lists of at most
+// kNoAllocMaxRayTiles = 40,960 tiles of 8x4 pixels): every image of up to
+// 1280 x 1024 pixels fits. That is 1.25 MiB, held on every GPU that loads the
+// library until the process exits. Images with more tiles are rejected with
+// TSDF_ERR_INVALID_ARG. All calls on a
 // device share the array and it keeps whatever the last call left in it; the
 // kernels clear both maps at the start of every call, so nothing depends on the
 // previous contents. Two calls whose work overlaps on the GPU (different
@@ -34,11 +36,14 @@
 
 namespace {
 constexpr int64_t kNoAllocMaxTiles = (1280 / tsdf::kRangeTile) * (1024 / tsdf::kRangeTile);
+constexpr int64_t kNoAllocMaxRayTiles = (1280 / 8) * (1024 / 4);
+constexpr int64_t kNoAllocWords = 2 * kNoAllocMaxTiles + tsdf::kRayBuckets * kNoAllocMaxRayTiles;
 constexpr int kMaxDevices = 64;
 }  // namespace
 
-// near map in the first kNoAllocMaxTiles words, far map in the second half
-static __device__ __align__(256) unsigned int tsdf_noalloc_range[2 * kNoAllocMaxTiles];
+// near map in the first kNoAllocMaxTiles words, far map in the next
+// kNoAllocMaxTiles, then the ray-order lists
+static __device__ __align__(256) unsigned int tsdf_noalloc_range[kNoAllocWords];
 
 namespace {
 
@@ -50,7 +55,9 @@ unsigned int* g_range_addr[kMaxDevices];   // device address of tsdf_noalloc_ran
 extern "C" tsdf_status tsdf_raycast_noalloc(tsdf_volume* v, const tsdf_intrinsics* K, const double pose_wc[16],
                                             float* depth_out, float* normal_out, float* vertex_out, void* stream) {
     if (!v || !tsdf::intrinsics_valid(K) || !tsdf::pose_valid(pose_wc)) return TSDF_ERR_INVALID_ARG;
-    if (tsdf::range_tiles(K->width, K->height) > kNoAllocMaxTiles) return TSDF_ERR_INVALID_ARG;
+    if (tsdf::range_tiles(K->width, K->height) > kNoAllocMaxTiles ||
+        tsdf::ray_tiles(K->width, K->height) > kNoAllocMaxRayTiles)
+        return TSDF_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSDF_ERR_CUDA;
     if (dev != v->device || dev < 0 || dev >= kMaxDevices) return TSDF_ERR_INVALID_ARG;
@@ -71,8 +78,9 @@ extern "C" tsdf_status tsdf_raycast_noalloc(tsdf_volume* v, const tsdf_intrinsic
     const tsdf::FrameParams p = tsdf::make_frame_params(v, *K, pose_wc);
     cudaStream_t st = (cudaStream_t)stream;
     v->last_stream = st;
-    const cudaError_t e = tsdf::launch_raycast_ranges(v, p, range, range + kNoAllocMaxTiles, depth_out, normal_out,
-                                                      vertex_out, st);
+    int* order = reinterpret_cast<int*>(range + 2 * kNoAllocMaxTiles);
+    const cudaError_t e = tsdf::launch_raycast_ranges(v, p, range, range + kNoAllocMaxTiles, order, depth_out,
+                                                      normal_out, vertex_out, st);
     if (e != cudaSuccess) {
         if (v->host_error == TSDF_OK) v->host_error = TSDF_ERR_CUDA;
         return TSDF_ERR_CUDA;

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
 // per-call ones restart (thread 0 of the call's first kernel).
 __device__ __forceinline__ void reset_rc_counters(Counters* ctr) {
     ctr->rc_next = 0;
+    for (int b = 0; b < kRayBuckets; ++b) ctr->rc_bucket[b] = 0;
     ctr->rays_total += ctr->rays_hit;
     ctr->rc_blocks_total += ctr->n_visible_rc;
     ctr->n_visible_rc = 0;
@@ -165,6 +166,51 @@ __global__ void __launch_bounds__(256) raster_kernel(const Counters* __restrict_
                 atomicMin(near_ + tile, zn_j);
                 atomicMax(far_ + tile, zf_j);
             }
+        }
+    }
+}
+
+// Ray order of the persistent raycast: one thread per 8x4-pixel ray tile (the
+// unit in which rays are handed out) takes the longest clipped range of its two
+// 4x4 range tiles and appends the tile to one of kRayBuckets lists, by that
+// length as a fraction of [raycast_near, raycast_far]: > 0.3, > 0.1, > 0.03,
+// the rest (and tiles with no range). The raycast hands out the lists in that
+// order, so the rays likely to march longest start first and the kernel's tail
+// is left with short ones. The order changes no result.
+__global__ void __launch_bounds__(256) ray_order_kernel(Counters* __restrict__ ctr, const unsigned int* __restrict__ near_,
+                                                        const unsigned int* __restrict__ far_, FrameParams p,
+                                                        int* __restrict__ order) {
+    pdl_prologue();
+    const int tiles_x = (p.width + 7) / 8, n = tiles_x * ((p.height + 3) / 4);
+    const int rtiles_x = (p.width + kRangeTile - 1) / kRangeTile;
+    const int lane = threadIdx.x & 31;
+    const float span = p.far_clip - p.near_clip;
+    for (int t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n; t0 += gridDim.x * blockDim.x) {
+        const int t = t0 + lane;
+        int b = kRayBuckets;
+        if (t < n) {
+            const int tx = t % tiles_x, ty = t / tiles_x;
+            float len = -1.0f;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int rx = 2 * tx + k;
+                if (rx < rtiles_x) {
+                    const float zn = __uint_as_float(near_[ty * rtiles_x + rx]);
+                    const float zf = __uint_as_float(far_[ty * rtiles_x + rx]);
+                    if (zn <= zf) len = fmaxf(len, fminf(zf, p.far_clip) - fmaxf(zn, p.near_clip));
+                }
+            }
+            const float f = len / span;
+            b = f > 0.3f ? 0 : f > 0.1f ? 1 : f > 0.03f ? 2 : 3;
+        }
+#pragma unroll
+        for (int k = 0; k < kRayBuckets; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, b == k);
+            if (!m) continue;
+            unsigned base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->rc_bucket[k], (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            if (b == k) order[(size_t)k * n + base + __popc(m & ((1u << lane) - 1u))] = t;
         }
     }
 }
@@ -586,10 +632,12 @@ __device__ __forceinline__ void refine_and_shade(const FrameParams& p, const int
 template <int kS, bool kNarrow>
 __global__ void __launch_bounds__(32 * kRcWarps, 8) raycast_persistent_kernel(
     const FrameParams p, const unsigned int* __restrict__ near_, const unsigned int* __restrict__ far_,
-    const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T, const unsigned int* __restrict__ occ2,
-    float* __restrict__ depth_out, float* __restrict__ normal_out,
+    const int* __restrict__ order, const int* __restrict__ table, const typename Codec<kS>::E* __restrict__ T,
+    const unsigned int* __restrict__ occ2, float* __restrict__ depth_out, float* __restrict__ normal_out,
     float* __restrict__ vertex_out, Counters* __restrict__ ctr) {
     pdl_prologue();
+    // ray tiles per bucket of the ray order (ray_order_kernel)
+    const unsigned nb0 = ctr->rc_bucket[0], nb1 = ctr->rc_bucket[1], nb2 = ctr->rc_bucket[2];
     // bracket queue of each warp: pix, z1, f1, z2, f2, dq (x, y, z)
     __shared__ float sq[kRcWarps][8][kQueue];
     float(*q)[kQueue] = sq[threadIdx.x >> 5];
@@ -638,7 +686,15 @@ __global__ void __launch_bounds__(32 * kRcWarps, 8) raycast_persistent_kernel(
                 rays_left = false;
                 continue;
             }
-            const unsigned t = idx >> 5, w = idx & 31u;
+            const unsigned w = idx & 31u;
+            // the idx / 32-th ray tile in bucket order
+            unsigned t = idx >> 5;
+            {
+                const unsigned n_t = n_rays >> 5;
+                unsigned b = 0;
+                if (t >= nb0) { t -= nb0; ++b; if (t >= nb1) { t -= nb1; ++b; if (t >= nb2) { t -= nb2; ++b; } } }
+                t = (unsigned)__ldg(order + (size_t)b * n_t + t);
+            }
             const unsigned ty = fast_div ? __umulhi(t, tdiv) : t / (unsigned)tiles_x;
             const unsigned tx = t - ty * (unsigned)tiles_x;
             const int u = (int)(tx * 8u + (w & 7u)), v = (int)(ty * 4u + (w >> 3));
@@ -790,7 +846,8 @@ void launch_march_t(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
 // Raycast tile shapes the autotuner chooses from (pixels per CTA, width x height).
 template <int kS, bool kNarrow>
 void launch_persistent(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
-                       float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+                       int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+    launch_pdl(ray_order_kernel, dim3(v->num_sms), dim3(256), st, v->ctr, near_, far_, p, order);
     // exactly the CTAs that fit at once: a CTA launched later would find no rays left
     static int per_sm = 0;
     if (per_sm == 0 &&
@@ -799,18 +856,18 @@ void launch_persistent(tsdf_volume* v, const FrameParams& p, const unsigned int*
          per_sm < 1))
         per_sm = 1;
     launch_pdl(raycast_persistent_kernel<kS, kNarrow>, dim3(v->num_sms * per_sm), dim3(32 * kRcWarps), st, p, near_,
-               far_, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, depth_out,
+               far_, (const int*)order, v->blk_slot, static_cast<const typename Codec<kS>::E*>(v->T), v->occ2, depth_out,
                normal_out, vertex_out, v->ctr);
 }
 
 template <int kS>
 void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
-                    float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+                    int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     if (v->lc.raycast_persistent) {
         if (v->cfg.block_capacity <= ((int64_t)1 << 23)) {
-            launch_persistent<kS, true>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            launch_persistent<kS, true>(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
         } else {
-            launch_persistent<kS, false>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            launch_persistent<kS, false>(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
         }
         return;
     }
@@ -828,16 +885,16 @@ void launch_march_s(tsdf_volume* v, const FrameParams& p, const unsigned int* ne
 }
 
 void launch_march(tsdf_volume* v, const FrameParams& p, const unsigned int* near_, const unsigned int* far_,
-                  float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+                  int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16:
-            launch_march_s<TSDF_STORAGE_F16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            launch_march_s<TSDF_STORAGE_F16>(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
             break;
         case TSDF_STORAGE_SNORM16:
-            launch_march_s<TSDF_STORAGE_SNORM16>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            launch_march_s<TSDF_STORAGE_SNORM16>(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
             break;
         default:
-            launch_march_s<TSDF_STORAGE_F32>(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+            launch_march_s<TSDF_STORAGE_F32>(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
             break;
     }
 }
@@ -852,7 +909,7 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
-    launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    launch_march(v, p, near_, far_, v->ray_order, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
 
@@ -928,12 +985,12 @@ cudaError_t launch_debug_slot(tsdf_volume* v, long long slot, float* sink, cudaS
 }
 
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
-                                  float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
+                                  int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const long long npix = range_tiles(p.width, p.height);
     launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
-    launch_march(v, p, near_, far_, depth_out, normal_out, vertex_out, st);
+    launch_march(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->visible_rc);
     cudaFree(v->ctr);
     cudaFree(v->range);
+    cudaFree(v->ray_order);
     cudaFree(v->dtiles);
     cudaFree(v->visible_batch);
     cudaFree(v->dtiles_batch);
@@ -220,14 +221,23 @@ cudaError_t ensure_batch(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t 
 }
 
 cudaError_t ensure_range(tsdf_volume* v, const tsdf_intrinsics& K, cudaStream_t st) {
-    const int64_t n = range_tiles(K.width, K.height);
-    if (n <= v->range_cap) return cudaSuccess;
+    const int64_t n = range_tiles(K.width, K.height), m = ray_tiles(K.width, K.height);
+    if (n <= v->range_cap && m <= v->ray_order_cap) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaFree(v->range);
-    v->range = nullptr;
-    v->range_cap = 0;
-    if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)n * sizeof(unsigned int));
-    if (e == cudaSuccess) v->range_cap = n;
+    if (e == cudaSuccess && n > v->range_cap) {
+        e = cudaFree(v->range);
+        v->range = nullptr;
+        v->range_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->range, 2 * (size_t)n * sizeof(unsigned int));
+        if (e == cudaSuccess) v->range_cap = n;
+    }
+    if (e == cudaSuccess && m > v->ray_order_cap) {
+        e = cudaFree(v->ray_order);
+        v->ray_order = nullptr;
+        v->ray_order_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&v->ray_order, (size_t)kRayBuckets * m * sizeof(int));
+        if (e == cudaSuccess) v->ray_order_cap = m;
+    }
     return e;
 }
 
