@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations the default line carries (batched K=8, capsules in three "
+                         "storage formats, FP16 + batched + learned against plain FP32)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--block-capacity", type=int, default=None, help="pool size in blocks")
     ap.add_argument("--mode", choices=["graph", "direct"], default="graph",
@@ -262,6 +265,37 @@ def ncu_traffic(stage, units):
     return rec["bytes_per_unit"] * units
 
 
+# L2 throughput of the persistent raycast kernel as a fraction of its peak (ncu
+# "L2 Cache Throughput", one capture of the room workload), with the hash of the
+# kernel source it was measured on; dropped when that source changes.
+NCU_L2 = {"raycast": {"sha": None, "frac": 0.15}}
+
+
+def ncu_l2_frac(stage):
+    rec = NCU_L2.get(stage)
+    src = os.path.join(ROOT, "paper_1311_7194_b300", "csrc", STAGE_SOURCES[stage])
+    if not rec or rec.get("sha") != _sha(src):
+        return None
+    return rec["frac"]
+
+
+def raycast_latency_model(steps_per_ray, rays, sec, sm_mhz, ctas_per_sm=8, threads=128):
+    """The raycast as a latency-bound loop: every ray is a chain of dependent
+    samples (steps_per_ray, traced), each a block-table load followed by its
+    voxel loads. With every resident lane (ctas_per_sm x threads per SM, the
+    persistent kernel's launch bounds) busy, a lane spends
+    sec x clock x lanes / (rays x steps) cycles per step: the figure to set
+    against two dependent L2-hit latencies, the cost of one step when a lane
+    never waits for its warp."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    lanes = n_sm * ctas_per_sm * threads
+    mhz = sm_mhz or 2032.0
+    cycles = sec * mhz * 1e6 * lanes / (rays * steps_per_ray)
+    return {"dependent_steps_per_ray": steps_per_ray, "rays": rays, "resident_lanes": lanes,
+            "cycles_per_step_per_lane": cycles, "sm_mhz": mhz}
+
+
 def raycast_algorithmic_bytes(counts, n_blocks, H, W):
     """Unique bytes one raycast must move: the distinct 32-byte sectors of T
     and of the block table its samples read, the block list read by the range
@@ -371,7 +405,7 @@ def run_ours(args):
     # per-frame work counts (one extra, untimed step, synchronising per frame);
     # every TRACE_EVERY-th frame's raycast is traced for its unique bytes
     vol.reset()
-    n_blocks, visible, updates, rc_bytes = [], [], [], []
+    n_blocks, visible, updates, rc_bytes, rc_steps = [], [], [], [], []
     for k in range(F):
         vol.allocate(depth_dev[k], seq.intr, seq.poses[k])
         vol.integrate(depth_dev[k], seq.intr, seq.poses[k])
@@ -380,6 +414,9 @@ def run_ours(args):
         if k % TRACE_EVERY == 0:
             c = vol.raycast_trace(seq.intr, seq.poses[k])
             rc_bytes.append(raycast_algorithmic_bytes(c, s_["n_blocks"], H, W))
+            # dependent samples along a ray: the march (jumps included), re-scans,
+            # the refinement, and one round for the six independent normal samples
+            rc_steps.append((c["march_samples"] + c["rescan_samples"] + c["refine_samples"]) / c["rays"] + 1.0)
     n_blocks, visible, updates = map(np.asarray, (n_blocks, visible, updates))
     peak, peak_kind = peaks()
     # integrate stage, algorithmic bytes per frame: read+write T and P of every
@@ -404,7 +441,13 @@ def run_ours(args):
                 "avg_launch_ms": 1000.0 * rc_sec,
                 "algorithmic_bytes": "distinct 32 B sectors of T and of the block table read (traced every "
                                      f"{TRACE_EVERY}th frame) + 16 B per allocated block (range cull) + "
-                                     "8 B per 4x4-pixel range tile + 28 B per pixel of maps written"}
+                                     "8 B per 4x4-pixel range tile + 28 B per pixel of maps written",
+                "limiter": "instruction issue and dependent-load latency, not bandwidth: DRAM and L2 run far below "
+                           "their peaks while the kernel runs (l2_frac_ncu), and the latency model below shows the "
+                           "cycles each dependent step costs a lane",
+                "l2_frac_ncu": ncu_l2_frac("raycast"),
+                "latency_model": raycast_latency_model(float(np.mean(rc_steps)), rays_per_step / F, rc_sec,
+                                                       clk.get("sm_mhz"))}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed_max / args.steps, "higher_is_better": True,
@@ -466,16 +509,68 @@ def run_ours(args):
                                 "fuse_s_per_frame": tf / args.cpu_frames, "raycast_s_per_frame": tr / args.cpu_frames,
                                 "rays_per_s": H * W * args.cpu_frames / tr}
     vol.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(run_extras(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def run_extras(args):
+    """The other configurations, each run after the room line with 3 warm-up
+    and 2 timed steps (CUDA events, inputs resident): the batched + graphed
+    workload (3000^3 grid of 1 mm voxels, 1000 frames, K = 8) with its integrate
+    roofline; the capsules (1280x1024, 4096^3 grid of 0.15 mm voxels, 200
+    frames) with T in FP32, FP16 and snorm16 and each one's error against the
+    FP64 oracle on 999 sampled voxels; and the FP16 + K = 8 + learned-variance
+    form against plain FP32 on the room sequence at a stated surface-error
+    bound."""
+    out = {}
+
+    def sub_args(**kw):
+        a = argparse.Namespace(**vars(args))
+        a.__dict__.update(dict(steps=2, warmup=3, block_capacity=None, no_autotune=args.no_autotune), **kw)
+        return a
+
+    def keep(d, keys):
+        return {k: d[k] for k in keys if k in d}
+
+    try:
+        b = run_batched(sub_args(frames=1000), emit=False)
+        out["batched_k8"] = keep(b, ["value", "unit", "ms_per_step", "config", "voxel_updates_per_s", "rays_per_s",
+                                     "work_per_step", "roofline_integrate_batch", "clocks"])
+    except Exception as e:          # the room line stands on its own
+        out["batched_k8"] = {"error": repr(e)}
+    caps = {}
+    for storage in ("f32", "f16", "snorm16"):
+        try:
+            c = run_capsules(sub_args(frames=200, workload="capsules", storage=storage, oracle_sample=999),
+                             emit=False)
+            caps[storage] = keep(c, ["value", "unit", "ms_per_step", "voxel_updates_per_s", "rays_per_s", "dtype",
+                                     "pool_bytes_per_voxel", "error_vs_fp64_oracle", "clocks"])
+        except Exception as e:
+            caps[storage] = {"error": repr(e)}
+    out["capsules"] = {"config": "capsules: 1280x1024, 4096^3 grid of 0.15 mm voxels, 200 frames, one graph per "
+                                 "frame", **caps}
+    try:
+        c = run_combined(sub_args(frames=300), emit=False)
+        out["vs_plain_fp32"] = {"config": c["config"], "forms": c["forms"], "speedup_vs_plain": c["speedup_vs_plain"],
+                                "surface_error_bound": c["surface_error_bound"], "clocks": c["clocks"]}
+    except Exception as e:
+        out["vs_plain_fp32"] = {"error": repr(e)}
+    return out
+
+
+def run_batched(args, emit=True):
     """The batched + graphed workload: 3000^3 grid of 1 mm voxels, 640x480,
     frames fused K = 8 per graph launch (tsdf_integrate_batch semantics) with a
-    raycast at each batch's last pose."""
+    raycast at each batch's last pose. The integrate stage's roofline: its
+    algorithmic bytes per launch are 16 B (T and P read and written once) per
+    voxel that any of the K frames updates, the K depth maps (4 B per pixel),
+    the block list read by the cull (16 B per block) and K visible-list entries
+    written and read per visible block (64 B each), over the stage's CUDA-event
+    duration in a second timed pass."""
     import numpy as np
     import torch
 
@@ -510,10 +605,33 @@ def run_batched(args):
         step()
     t1.record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
     sec = t0.elapsed_time(t1) / 1000.0
     st = vol.stats()
     vol.check()
+    # stage times: the same steps again with event nodes at the stage boundaries
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(F // K)] for _ in range(args.steps)]
+    for s in range(args.steps):
+        vol.reset()
+        for b, k in enumerate(range(0, F, K)):
+            g.set_events(ev[s][b])
+            g.launch([depth_dev[k + j] for j in range(K)], seq.poses[k:k + K], maps)
+        g.set_events(None)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    integ_ms = sum(ev[s][b][1].elapsed_time(ev[s][b][2]) for s in range(args.steps) for b in range(F // K)) / args.steps
+    peak, peak_kind = peaks()
+    launches = F // K
+    touched, nblk = st["voxels_touched_total"], st["n_blocks"]
+    # algorithmic bytes per step, with each launch's own pool size and visible
+    # count (one more untimed step, read back after every launch)
+    integ_bytes = 0.0
+    vol.reset()
+    for k in range(0, F, K):
+        g.launch([depth_dev[k + j] for j in range(K)], seq.poses[k:k + K], maps)
+        s_ = vol.stats()
+        integ_bytes += K * 4.0 * H * W + 16.0 * s_["n_blocks"] + 64.0 * K * s_["visible_blocks"]
+    integ_bytes += 16.0 * touched
+    achieved = integ_bytes / (integ_ms / 1000.0) / 1e9
     line = {"metric": METRIC, "value": F * args.steps / sec, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -521,14 +639,50 @@ def run_batched(args):
                                    "graph launch, raycast per batch", "frames_per_step": F},
             "voxel_updates_per_s": st["voxel_updates_total"] * args.steps / sec,
             "rays_per_s": (F // K) * H * W * args.steps / sec,
-            "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "blocks": int(st["n_blocks"])},
+            "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "voxels_touched": int(touched),
+                              "blocks": int(nblk)},
+            "roofline_integrate_batch": {"kernel": f"integrate stage of a K={K} launch (K depth tiles + batched cull "
+                                                   "+ batched Alg. 3 integrate)", "bound": "hbm",
+                                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                         "peak_kind": peak_kind, "traffic": None,
+                                         "algorithmic_bytes_per_launch": integ_bytes / launches,
+                                         "avg_launch_ms": integ_ms / launches},
             "graph_instantiations": g.instantiations, "clocks": clk}
     g.close()
     vol.close()
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_capsules(args):
+_CAPSULE_ORACLE = {}
+
+
+def capsule_oracle_reference(seq, n_sample):
+    """Sampled voxels of the capsule sequence replayed by the FP64 oracle (the
+    same for every storage format, so computed once): block allocation over the
+    whole sequence, n_sample voxels drawn from the allocated blocks, and their T
+    after every frame from their block's allocation frame on."""
+    import numpy as np
+    import oracle
+    key = (seq.depth.shape, n_sample)
+    if key not in _CAPSULE_ORACLE:
+        oracle.build()
+        ov = oracle.OracleVolume(seq.volume, seq.intr, store_values=False)
+        for k in range(seq.depth.shape[0]):
+            ov.allocate(seq.depth[k], seq.poses[k], k)
+        oe = ov.export(values=False)
+        rng = np.random.default_rng(11)
+        pick = rng.choice(oe.coords.shape[0], size=min(n_sample, oe.coords.shape[0]), replace=False)
+        local = rng.integers(0, 512, size=pick.size)
+        vox = oe.coords[pick] * 8 + np.stack([local & 7, (local >> 3) & 7, local >> 6], -1)
+        T, P, amb = oracle.replay_voxels(seq.volume, seq.intr, list(seq.depth), seq.poses, vox,
+                                         oe.alloc_frame[pick], amb_px=5e-4)
+        _CAPSULE_ORACLE[key] = (oe.coords[pick], local, T, amb)
+    return _CAPSULE_ORACLE[key]
+
+
+def run_capsules(args, emit=True):
     """Small scenes, one graph launch per frame, T stored as float32, FP16 or
     snorm16 (P float32); optionally the error of sampled voxels against the
     FP64 oracle. capsules: high-resolution small object, 1280x1024, 4096^3 grid
@@ -589,22 +743,11 @@ def run_capsules(args):
             "pool_bytes_per_voxel": 4 + (4 if storage == tsdf.STORAGE_F32 else 2),
             "algorithmic_bytes_per_update": bytes_per_update, "clocks": clk}
     if args.oracle_sample > 0:
-        import oracle
-        oracle.build()
-        ov = oracle.OracleVolume(seq.volume, seq.intr, store_values=False)
-        for k in range(F):
-            ov.allocate(seq.depth[k], seq.poses[k], k)
-        oe = ov.export(values=False)
-        rng = np.random.default_rng(11)
-        pick = rng.choice(oe.coords.shape[0], size=min(args.oracle_sample, oe.coords.shape[0]), replace=False)
-        local = rng.integers(0, 512, size=pick.size)
-        vox = oe.coords[pick] * 8 + np.stack([local & 7, (local >> 3) & 7, local >> 6], -1)
-        T, P, amb = oracle.replay_voxels(seq.volume, seq.intr, list(seq.depth), seq.poses, vox,
-                                         oe.alloc_frame[pick], amb_px=5e-4)
+        ocoords, local, T, amb = capsule_oracle_reference(seq, args.oracle_sample)
         ge = vol.export()
         nb = seq.volume.grid_dim // 8
         keys = ge.coords[:, 0].astype(np.int64) + nb * (ge.coords[:, 1] + nb * ge.coords[:, 2].astype(np.int64))
-        okeys = oe.coords[pick, 0].astype(np.int64) + nb * (oe.coords[pick, 1] + nb * oe.coords[pick, 2].astype(np.int64))
+        okeys = ocoords[:, 0].astype(np.int64) + nb * (ocoords[:, 1] + nb * ocoords[:, 2].astype(np.int64))
         order = np.argsort(keys)
         slot = order[np.searchsorted(keys[order], okeys)]
         gT = ge.T[slot, local].astype(np.float64)
@@ -615,7 +758,9 @@ def run_capsules(args):
                                         "chi_mismatch": int(((np.isnan(T) != np.isnan(gT)) & ~amb).sum())}
     pipe.graph.close()
     vol.close()
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_tracking(args):
@@ -749,7 +894,7 @@ def run_mesh(args):
     print(json.dumps(line), flush=True)
 
 
-def run_combined(args):
+def run_combined(args, emit=True):
     """The plain FP32 method against the form that stores T as FP16, fuses K = 8
     frames per graph launch and takes its measurement variances from the learned
     network, on the same GPU and sequence: the room (640x480, 2048^3 grid of
@@ -838,7 +983,9 @@ def run_combined(args):
                                     "met": comb["surface_error_mm"]["mean_abs"]
                                     <= bound * plain["surface_error_mm"]["mean_abs"]},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_shift(args):

@@ -125,6 +125,10 @@ typedef struct {
     int64_t visible_blocks_total;
     int64_t rays_hit_total;
     int64_t raycast_blocks_total;
+    int64_t voxels_touched_total;  /* voxels whose T and P an integrate call read and wrote (updated by at
+                                      least one of its frames), summed over calls: the unit of the
+                                      integrate roofline; equals voxel_updates_total when every call
+                                      fuses one frame */
 } tsdf_stats;
 
 /* Fill *cfg with the defaults listed in tsdf_config. Host only. */

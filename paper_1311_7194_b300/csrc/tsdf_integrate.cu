@@ -91,8 +91,10 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
 __device__ __forceinline__ void reset_frame_counters(Counters* ctr) {
     ctr->updates_total += ctr->voxel_updates;
     ctr->visible_total += ctr->n_visible;
+    ctr->touched_total += ctr->voxels_touched;
     ctr->n_visible = 0;
     ctr->voxel_updates = 0;
+    ctr->voxels_touched = 0;
 }
 
 // Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
@@ -457,7 +459,10 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
         }
     }
     updates = warp_sum(updates);
-    if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+    if ((threadIdx.x & 31) == 0 && updates) {
+        atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+        atomicAdd(&ctr->voxels_touched, (unsigned long long)updates);   // one frame: each update touches a voxel once
+    }
 }
 
 // K frames in one pass: T and P of a voxel are loaded once (at its first valid
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
     const unsigned nvis = ctr->n_visible;
     const int v0 = threadIdx.x * 4;
     const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
-    unsigned updates = 0;
+    unsigned updates = 0, touched = 0;
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
         const VisibleBlock* ve = vis + (size_t)i * kMaxBatch;
         const int slot = ve[0].slot;
@@ -484,6 +489,7 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
         const size_t off = (size_t)slot * kBlockVoxels + (size_t)v0;
         float tv[4], pv[4];
         bool loaded = false;
+        unsigned hit = 0;    // bit e: voxel e updated by some frame of the batch
         for (int k = max(first, 0); k < bp.K; ++k) {
             const FrameParams& p = bp.fp[k];
             const VisibleBlock vb = ve[k];
@@ -512,9 +518,11 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
                 if (ok[e]) {
                     update<kRule>(p, tv[e], pv[e], tk[e], pk[e]);
                     ++updates;
+                    hit |= 1u << e;
                 }
             }
         }
+        touched += (unsigned)__popc(hit);
         if (loaded) {
             Codec<kS>::store4(T + off, tv, bp.fp[0].tsc);
             if (kRule != TSDF_UPDATE_AVERAGE)
@@ -522,7 +530,11 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
         }
     }
     updates = warp_sum(updates);
-    if ((threadIdx.x & 31) == 0 && updates) atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+    touched = warp_sum(touched);
+    if ((threadIdx.x & 31) == 0 && updates) {
+        atomicAdd(&ctr->voxel_updates, (unsigned long long)updates);
+        atomicAdd(&ctr->voxels_touched, (unsigned long long)touched);
+    }
 }
 
 

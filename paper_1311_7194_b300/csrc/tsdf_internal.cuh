@@ -52,6 +52,8 @@ struct Counters {
     unsigned int rc_next;        // next ray handed out by the persistent raycast
     unsigned int pad2;
     unsigned int rc_bucket[kRayBuckets];   // 8x4-pixel ray tiles per range-length bucket (ray order)
+    unsigned long long voxels_touched;     // voxels updated by at least one frame of the current call
+    unsigned long long touched_total;
 };
 
 // One visible block for the integrate kernel: pool slot, the camera-space

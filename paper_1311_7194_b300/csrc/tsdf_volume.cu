@@ -652,6 +652,7 @@ tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* out) {
     out->visible_blocks_total = (int64_t)(c.visible_total + c.n_visible);
     out->rays_hit_total = (int64_t)(c.rays_total + c.rays_hit);
     out->raycast_blocks_total = (int64_t)(c.rc_blocks_total + c.n_visible_rc);
+    out->voxels_touched_total = (int64_t)(c.touched_total + c.voxels_touched);
     return TSDF_OK;
 }
 

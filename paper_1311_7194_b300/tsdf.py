@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
                 ("raycast_blocks", ctypes.c_int64), ("rays_hit", ctypes.c_int64),
                 ("frames", ctypes.c_int64), ("voxel_updates_total", ctypes.c_int64),
                 ("visible_blocks_total", ctypes.c_int64), ("rays_hit_total", ctypes.c_int64),
-                ("raycast_blocks_total", ctypes.c_int64)]
+                ("raycast_blocks_total", ctypes.c_int64), ("voxels_touched_total", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

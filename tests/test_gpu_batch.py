@@ -56,6 +56,11 @@ def _assert_same(a, b):
     assert np.array_equal(ea.P.view(np.uint32)[~chi], eb.P.view(np.uint32)[~chi]), "P differs"
     sa, sb = a.stats(), b.stats()
     assert sa["frames"] == sb["frames"] and sa["voxel_updates_total"] == sb["voxel_updates_total"]
+    # voxels touched (a: one frame per call, b: K frames per call): every update
+    # of a one-frame call touches its voxel once; a K-frame call touches each
+    # voxel it updates once, however many of its frames update it (at most 8)
+    assert sa["voxels_touched_total"] == sa["voxel_updates_total"]
+    assert sb["voxel_updates_total"] / 8 <= sb["voxels_touched_total"] <= sb["voxel_updates_total"]
     return ea
 
 
