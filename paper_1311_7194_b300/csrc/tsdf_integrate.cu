@@ -40,14 +40,44 @@ namespace {
 
 constexpr int kIntegrateThreads = 128;
 
-__device__ __forceinline__ void cam_block_origin(const FrameParams& p, int4 bc, double o[3]) {
-    const double x = p.origin[0] + (double)(kSide * bc.x) * p.s - p.t[0];
-    const double y = p.origin[1] + (double)(kSide * bc.y) * p.s - p.t[1];
-    const double z = p.origin[2] + (double)(kSide * bc.z) * p.s - p.t[2];
-    // camera coordinates R^T (X - t)
-    o[0] = p.R[0] * x + p.R[3] * y + p.R[6] * z;
-    o[1] = p.R[1] * x + p.R[4] * y + p.R[7] * z;
-    o[2] = p.R[2] * x + p.R[5] * y + p.R[8] * z;
+// Error-free transformations of float arithmetic (Knuth's two-sum, and the
+// product by a fused multiply-add): a + b = s + e and a b = p + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Camera position of the block's voxel (0,0,0), R^T (origin + 8 b s - t) =
+// oc0 + sum_a (8 b_a) cs[., a], in float-float arithmetic: oc0 and cs are
+// carried as float pairs rounded once from double on the host, each product
+// 8 b_a cs is exact (two_prod), and the sums keep their rounding errors
+// (two_sum), so the pair (o, lo) holds the double value to about 2^-48 of its
+// size (4e-14 m at room scale, far below the 1e-12 m the hi/lo split of z
+// needs). o is that value's nearest float. On sm_103a this replaces double
+// arithmetic, whose throughput is a small fraction of float's.
+__device__ __forceinline__ void cam_block_origin(const FrameParams& p, int4 bc, float o[3], float* z_lo) {
+    const float m[3] = {(float)(kSide * bc.x), (float)(kSide * bc.y), (float)(kSide * bc.z)};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float sh = p.oc0[r], sl = p.oc0_lo[r];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float ph, pl, s, e;
+            two_prod(m[a], p.cs[3 * r + a], ph, pl);
+            pl = __fmaf_rn(m[a], p.cs_lo[3 * r + a], pl);
+            two_sum(sh, ph, s, e);
+            e = __fadd_rn(e, __fadd_rn(sl, pl));
+            two_sum(s, e, sh, sl);
+        }
+        o[r] = sh;
+        if (r == 2) *z_lo = sl;
+    }
 }
 
 // Conservative visibility of the box spanning voxel offsets [lo, hi] of a block
@@ -191,8 +221,8 @@ __device__ __forceinline__ bool band_reachable(const FrameParams& p, const float
 __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* __restrict__ tiles, int4 bc, int slot,
                                            VisibleBlock* e) {
     // visibility from a float32 camera position of the block's first voxel
-    // (a few ulps from the double one: far inside the pixel of padding and the
-    // band slack); the double position only for blocks that pass
+    // (a few ulps from the exact one: far inside the pixel of padding and the
+    // band slack); the float-float position only for blocks that pass
     float of[3];
     const float bx = (float)(kSide * bc.x), by = (float)(kSide * bc.y), bz = (float)(kSide * bc.z);
 #pragma unroll
@@ -203,15 +233,10 @@ __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* _
     bool keep = box_visible(p, of, 0.0f, (float)(kSide - 1), p.zlo, p.zhi, 1.0f, &zmin, &zmax, rect);
     if (keep && rect[0] > -1e29f) keep = band_reachable(p, tiles, rect, zmin, zmax, &zlo, &zhi);
     e->slot = slot;
-    double oz = (double)of[2];
-    if (keep) {
-        double o[3];
-        cam_block_origin(p, bc, o);
-        for (int r = 0; r < 3; ++r) of[r] = (float)o[r];
-        oz = o[2];
-    }
+    float oz_lo = 0.0f;
+    if (keep) cam_block_origin(p, bc, of, &oz_lo);
     for (int r = 0; r < 3; ++r) e->o[r] = of[r];
-    e->oz_lo = (float)(oz - (double)of[2]);
+    e->oz_lo = oz_lo;
     e->zlo = keep ? zlo : 3.0e38f;     // an empty range makes every voxel chi
     e->zhi = keep ? zhi : -3.0e38f;
     e->pad = 0;

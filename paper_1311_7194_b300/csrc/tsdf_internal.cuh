@@ -94,6 +94,8 @@ struct FrameParams {
     float Rs[9];         // R / s (world voxel units per camera unit)
     float q0[3];         // (t - origin) / s
     float oc0[3];        // camera position of voxel (0,0,0): R^T (origin - t)
+    float oc0_lo[3];     // oc0 in double minus oc0: (oc0, oc0_lo) carry the double value as a float pair
+    float cs_lo[9];      // likewise the low parts of cs
     float fx, fy, cx, cy, cxh, cyh;   // cxh = cx + 1/2
     float depth_min, depth_max;
     float delta, Q, sigma_coeff;

@@ -136,13 +136,18 @@ FrameParams make_frame_params(const tsdf_volume* v, const tsdf_intrinsics& K, co
     p.s = s;
     for (int r = 0; r < 3; ++r)
         for (int a = 0; a < 3; ++a) {
-            p.cs[3 * r + a] = (float)(s * p.R[3 * a + r]);
+            const double c = s * p.R[3 * a + r];
+            p.cs[3 * r + a] = (float)c;
+            p.cs_lo[3 * r + a] = (float)(c - (double)p.cs[3 * r + a]);
             p.Rs[3 * r + a] = (float)(p.R[3 * r + a] / s);
         }
     for (int r = 0; r < 3; ++r) p.q0[r] = (float)((p.t[r] - p.origin[r]) / s);
-    for (int r = 0; r < 3; ++r)
-        p.oc0[r] = (float)(p.R[r] * (p.origin[0] - p.t[0]) + p.R[3 + r] * (p.origin[1] - p.t[1]) +
-                           p.R[6 + r] * (p.origin[2] - p.t[2]));
+    for (int r = 0; r < 3; ++r) {
+        const double o = p.R[r] * (p.origin[0] - p.t[0]) + p.R[3 + r] * (p.origin[1] - p.t[1]) +
+                         p.R[6 + r] * (p.origin[2] - p.t[2]);
+        p.oc0[r] = (float)o;
+        p.oc0_lo[r] = (float)(o - (double)p.oc0[r]);
+    }
     p.fx = K.fx; p.fy = K.fy; p.cx = K.cx; p.cy = K.cy;
     p.cxh = (float)((double)K.cx + 0.5);
     p.cyh = (float)((double)K.cy + 0.5);
