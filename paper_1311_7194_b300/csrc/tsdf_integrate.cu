@@ -318,10 +318,6 @@ __device__ __forceinline__ float rcp_newton(float x) {
     return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
 }
 
-// Projective measurement T_k of one voxel (Fusion: project x onto the depth map,
-// distance to the measured point; chi when there is no measurement). The voxel
-// is lx steps along the block's x rows from a row start whose camera position
-// is (xr, yr, o_z + zr); zr carries the low part of o_z.
 // T_k refined by Gauss-Newton steps in the depth map (section "Integration of
 // Measurements", last paragraph): the measured surface is the depth map
 // back-projected with bilinear depth, S(u, v) = D~(u, v) ((u - cx)/fx,
@@ -373,34 +369,53 @@ __device__ __forceinline__ float refine_tk(const FrameParams& p, const float* __
     return dist < 0.0f ? t0 : side * dist;
 }
 
-// kZRange: voxels outside the entry's camera-z range [zlo, zhi] also fail the
-// flag (batched kernel); in the single-frame kernel that range rejects few
-// voxels, and the band test alone decides.
+// The projective measurement T_k of two neighbouring voxels of a row (Fusion:
+// project x onto the depth map, distance to the measured point; chi when there
+// is no measurement), at x offsets lx and lx + 1 from a row start whose camera
+// position is (xr, yr, o_z + zr); zr carries the low part of o_z. kZRange:
+// voxels outside the entry's camera-z range [zlo, zhi] also fail the flag
+// (batched kernel); in the single-frame kernel that range rejects few voxels,
+// and the band test alone decides. The nearest pixel is floor(u + 1/2) in
+// [0, W), found without a branch: a voxel that fails a test still loads pixel
+// 0 and is rejected by the flag (for z <= 1e-30, u and v may be infinite or
+// NaN; the flag drops them). Computed with sm_100's paired float
+// instructions, each of which rounds both elements exactly as its scalar
+// counterpart, so half the floating-point instructions are issued.
 template <bool kRefine, bool kZRange = true>
-__device__ __forceinline__ bool measure(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
-                                        float zr, const float2* __restrict__ meas, const float* __restrict__ depth,
-                                        float* Tk, float* pk) {
-    const float zs = __fmaf_rn(lx, p.cs[6], zr);
-    const float z = __fadd_rn(vb.o[2], zs);
-    const float x = __fmaf_rn(lx, p.cs[0], xr);
-    const float y = __fmaf_rn(lx, p.cs[3], yr);
-    const float rz = rcp_newton(z);
-    const float uf = __fmaf_rn(p.fx, __fmul_rn(x, rz), p.cxh);   // u + 1/2
-    const float vf = __fmaf_rn(p.fy, __fmul_rn(y, rz), p.cyh);
-    // nearest pixel: floor(u + 1/2) in [0, W). Without a branch: a voxel that
-    // fails a test still loads pixel 0 and is rejected by the flag (for
-    // z <= 1e-30, u and v may be infinite or NaN; the flag drops them).
-    const int ui = __float2int_rd(uf), vi = __float2int_rd(vf);
-    bool ok = (z > 1e-30f) & ((unsigned)ui < (unsigned)p.width) & ((unsigned)vi < (unsigned)p.height);
-    if (kZRange) ok &= (z >= vb.zlo) & (z <= vb.zhi);
-    const int pix = ok ? vi * p.width + ui : 0;
-    const float2 m = __ldg(meas + pix);               // (D or NaN, p_k)
-    const float t = __fsub_rn(__fsub_rn(m.x, vb.o[2]), zs);
-    ok &= fabsf(t) <= p.delta;                        // false for a NaN D
-    *Tk = t;
-    if (kRefine && ok) *Tk = refine_tk(p, depth, x, y, vb.o[2], zs, uf - 0.5f, vf - 0.5f, t);
-    *pk = m.y;
-    return ok;
+__device__ __forceinline__ void measure2(const FrameParams& p, const VisibleBlock& vb, float lx, float xr, float yr,
+                                         float zr, const float2* __restrict__ meas, const float* __restrict__ depth,
+                                         float* Tk, float* pk, bool* ok) {
+    const float2 L = make_float2(lx, lx + 1.0f);
+    const float2 zs = __ffma2_rn(L, make_float2(p.cs[6], p.cs[6]), make_float2(zr, zr));
+    const float2 z = __fadd2_rn(make_float2(vb.o[2], vb.o[2]), zs);
+    const float2 x = __ffma2_rn(L, make_float2(p.cs[0], p.cs[0]), make_float2(xr, xr));
+    const float2 y = __ffma2_rn(L, make_float2(p.cs[3], p.cs[3]), make_float2(yr, yr));
+    // 1/z: hardware approximation refined by one Newton-Raphson step, as rcp_newton
+    float2 rz = make_float2(rcp_approx(z.x), rcp_approx(z.y));
+    const float2 err = __ffma2_rn(make_float2(-z.x, -z.y), rz, make_float2(1.0f, 1.0f));
+    rz = __ffma2_rn(rz, err, rz);
+    const float2 uf = __ffma2_rn(make_float2(p.fx, p.fx), __fmul2_rn(x, rz), make_float2(p.cxh, p.cxh));
+    const float2 vf = __ffma2_rn(make_float2(p.fy, p.fy), __fmul2_rn(y, rz), make_float2(p.cyh, p.cyh));
+    const float zv[2] = {z.x, z.y}, uv[2] = {uf.x, uf.y}, vv[2] = {vf.x, vf.y};
+    float2 m[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int ui = __float2int_rd(uv[e]), vi = __float2int_rd(vv[e]);
+        ok[e] = (zv[e] > 1e-30f) & ((unsigned)ui < (unsigned)p.width) & ((unsigned)vi < (unsigned)p.height);
+        if (kZRange) ok[e] &= (zv[e] >= vb.zlo) & (zv[e] <= vb.zhi);
+        m[e] = __ldg(meas + (ok[e] ? vi * p.width + ui : 0));   // (D or NaN, p_k)
+    }
+    const float2 t = __fadd2_rn(__fadd2_rn(make_float2(m[0].x, m[1].x), make_float2(-vb.o[2], -vb.o[2])),
+                                make_float2(-zs.x, -zs.y));
+    const float tv[2] = {t.x, t.y}, xv[2] = {x.x, x.y}, yv[2] = {y.x, y.y}, zsv[2] = {zs.x, zs.y};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        ok[e] &= fabsf(tv[e]) <= p.delta;                 // false for a NaN D
+        Tk[e] = tv[e];
+        if (kRefine && ok[e])
+            Tk[e] = refine_tk(p, depth, xv[e], yv[e], vb.o[2], zsv[e], uv[e] - 0.5f, vv[e] - 0.5f, tv[e]);
+        pk[e] = m[e].y;
+    }
 }
 
 // One measurement into one voxel, chi is NaN; kRule is a tsdf_update_rule.
@@ -455,10 +470,10 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
         bool ok[kVPT];
         bool any = false;
 #pragma unroll
-        for (int e = 0; e < kVPT; ++e) {
-            ok[e] = measure<kRefine, false>(p, vb, lx0 + (float)e, xr, yr, zr, meas, depth, &tk[e], &pk[e]);
-            any |= ok[e];
-        }
+        for (int e = 0; e < kVPT; e += 2)
+            measure2<kRefine, false>(p, vb, lx0 + (float)e, xr, yr, zr, meas, depth, &tk[e], &pk[e], &ok[e]);
+#pragma unroll
+        for (int e = 0; e < kVPT; ++e) any |= ok[e];
         if (!any) continue;
         const size_t off = (size_t)vb.slot * kBlockVoxels + (size_t)v0;
         float tv[kVPT], pv[kVPT];
@@ -526,10 +541,10 @@ __global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Coun
             bool ok[4];
             bool any = false;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                ok[e] = measure<kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, bp.meas[k], bp.depth[k], &tk[e], &pk[e]);
-                any |= ok[e];
-            }
+            for (int e = 0; e < 4; e += 2)
+                measure2<kRefine>(p, vb, lx0 + (float)e, xr, yr, zr, bp.meas[k], bp.depth[k], &tk[e], &pk[e], &ok[e]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) any |= ok[e];
             if (!any) continue;
             if (!loaded) {
                 Codec<kS>::load4(T + off, tv, bp.fp[0].tsc);
