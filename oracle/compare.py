@@ -58,6 +58,7 @@ def compare_values(gT, gP, oT, oP, amb, delta, tol_T=1e-5, tol_P=1e-5) -> dict:
         "ambiguous_valid_frac": float((amb & ~o_chi).sum() / max(1, (~o_chi).sum())),
         "chi_mismatch": chi_mismatch,
         "max_dT_over_delta": float(dT.max() / delta) if dT.size else 0.0,
+        "q999_dT_over_delta": float(np.quantile(dT, 0.999) / delta) if dT.size else 0.0,
         "max_rel_dP": float(rP.max()) if rP.size else 0.0,
         "ok": bool(chi_mismatch == 0 and (dT.size == 0 or dT.max() <= tol_T * delta)
                    and (rP.size == 0 or rP.max() <= tol_P)),

@@ -1161,7 +1161,10 @@ void ov_mlp_loss_grad(const double* w, int64_t n, const double* feat, const doub
 }
 
 // Per-pixel variance map with the network (float output, 0 where the depth is
-// not valid): p_quad exp(out), or p_quad where |out| > ln 4 or not finite.
+// not valid): p_quad exp(out), or p_quad where out lies outside
+// [-ln 4, ln 64] or is not finite (a measurement may be up to 64 times noisier
+// than the quadratic model says - a sensor far poorer at depth edges - or 4
+// times less noisy).
 void ov_mlp_variance_map(const double* w, const float* depth, const ov_intr* in, const ov_params* p, float* var) {
     const int64_t n = (int64_t)in->width * in->height;
     std::vector<int32_t> uv(2 * n);
@@ -1173,7 +1176,7 @@ void ov_mlp_variance_map(const double* w, const float* depth, const ov_intr* in,
     std::vector<uint8_t> valid(n);
     ov_mlp_features(depth, in, p, n, uv.data(), feat.data(), valid.data());
     ov_mlp_forward(w, n, feat.data(), out.data());
-    const double lim = std::log(4.0);
+    const double lo = -std::log(4.0), hi = std::log(64.0);
     for (int64_t k = 0; k < n; ++k) {
         if (!valid[k]) {
             var[k] = 0.0f;
@@ -1182,7 +1185,7 @@ void ov_mlp_variance_map(const double* w, const float* depth, const ov_intr* in,
         const double d = (double)depth[k];
         const double sg = (double)p->sigma_coeff * d * d;
         const double pq = sg * sg;
-        var[k] = (float)((std::isfinite(out[k]) && std::fabs(out[k]) <= lim) ? pq * std::exp(out[k]) : pq);
+        var[k] = (float)((std::isfinite(out[k]) && out[k] >= lo && out[k] <= hi) ? pq * std::exp(out[k]) : pq);
     }
 }
 

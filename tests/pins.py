@@ -587,7 +587,8 @@ def pin_mlp_features_on_planes(lib_path=None):
 
 def pin_mlp_variance_fallback(lib_path=None):
     """Variance = p_quad exp(out): the zero network gives the quadratic model,
-    b3 = 0.5 scales it by e^0.5, and an output beyond ln 4 falls back to it."""
+    b3 = 0.5 scales it by e^0.5, outputs inside [-ln 4, ln 64] scale it by
+    e^out, and an output outside that range falls back to it."""
     W, H = 16, 12
     intr = synth.Intrinsics.centred(14.0, W, H)
     vol = _plane_volume(sigma=1.5e-3)
@@ -595,7 +596,8 @@ def pin_mlp_variance_fallback(lib_path=None):
     depth[3, 4] = 0.0
     n = int(oracle.lib(lib_path).ov_mlp_param_count())
     pq = ((np.float64(np.float32(1.5e-3)) * depth.astype(np.float64) ** 2) ** 2)
-    for b3, scale in ((0.0, 1.0), (0.5, np.exp(0.5)), (2.0, 1.0), (-1.5, 1.0)):
+    for b3, scale in ((0.0, 1.0), (0.5, np.exp(0.5)), (2.0, np.exp(2.0)), (4.0, np.exp(4.0)), (-1.0, np.exp(-1.0)),
+                      (4.3, 1.0), (-1.5, 1.0)):
         w = np.zeros(n)
         w[-1] = b3
         var = oracle.Mlp(w, lib_path).variance_map(depth, intr, vol).astype(np.float64)

@@ -40,11 +40,16 @@ def test_refined_tk_matches_oracle():
     r = compare.compare_blocks(ge.coords, ge.alloc_frame, oe.coords, oe.alloc_frame, nb)
     assert r["keys_equal"] and r["frames_equal"], r
     _, _, gT, gP = compare.sort_by_key(ge.coords, ge.alloc_frame, ge.T, ge.P, nb)
-    # the lateral camera coordinates enter |S - X| in float (no hi/lo split), a
-    # few 1e-7 m at 2 m, and three float Gauss-Newton steps stop a little apart
-    # from the double ones: 2e-4 delta (6 um here) rather than 1e-5
+    # Three Gauss-Newton steps in float stop a little apart from the double
+    # ones: the same steps in float32 and float64 on these frames differ by a
+    # median 1e-6 delta, 1e-5 delta at the 99.9th percentile and up to 4e-4
+    # delta where a step is ill-conditioned, whether or not the lateral
+    # coordinates carry a low part (a float32 emulation of the steps against
+    # float64). The bar is that floor: 2e-4 delta at most, 3e-5 delta at the
+    # 99.9th percentile.
     v = compare.compare_values(gT, gP, oe.T, oe.P, oe.amb, seq.volume.truncation, tol_T=2e-4)
     assert v["ok"], json.dumps(v)
+    assert v["q999_dT_over_delta"] <= 3e-5, json.dumps(v)
     assert v["compared"] > 100000 and v["ambiguous_valid_frac"] < 0.2, json.dumps(v)
 
 

@@ -67,7 +67,8 @@ MUTATIONS = [
      "? std::fmax(-1.0, std::fmin(1.0, (d - d0) / delta)) : 0.0;"),
     ("mlp_depth_feature", "f[25] = d0 / 4.0;", "f[25] = d0 / 2.0;"),
     ("mlp_variance_exp_sign", "pq * std::exp(out[k])", "pq * std::exp(-out[k])"),
-    ("mlp_fallback_limit", "const double lim = std::log(4.0);", "const double lim = std::log(16.0);"),
+    ("mlp_fallback_limit", "lo = -std::log(4.0), hi = std::log(64.0);", "lo = -std::log(4.0), hi = std::log(16.0);"),
+    ("mlp_fallback_low_limit", "lo = -std::log(4.0), hi = std::log(64.0);", "lo = -std::log(16.0), hi = std::log(64.0);"),
     ("mlp_first_layer_relu", "t->a1[j] = acc > 0.0 ? acc : 0.0;", "t->a1[j] = acc;"),
     ("shift_origin_sign", "v.p.origin[r] += (double)((int64_t)M * d[r]) * (double)v.p.voxel_size;",
      "v.p.origin[r] -= (double)((int64_t)M * d[r]) * (double)v.p.voxel_size;"),
