@@ -472,7 +472,7 @@ tsdf_status tsdf_mlp_features(const tsdf_volume* vol, const float* depth, const 
                               const int32_t* uv, float* feats, uint8_t* valid, void* stream);
 /* Training pairs: for pixels where both the measured depth and the model's
  * raycast depth pred_depth (same pose; 0 = miss) are valid and the residual
- * r = depth - pred lies within the truncation band, append the features and
+ * r = depth - pred lies within 4 truncation distances, append the features and
  * s = r^2 / p_quad at *count (device counter, incremented; rows beyond max_n
  * are counted but not written). */
 tsdf_status tsdf_mlp_harvest(const tsdf_volume* vol, const float* depth, const float* pred_depth,

@@ -18,7 +18,9 @@
 //       variance_mlp_kernel writes the same p_k as a map (tsdf_mlp_variance).
 //   harvest_kernel: training pairs from a measured depth map and the model's
 //       raycast at the same pose: features and s = r^2 / p_quad for pixels whose
-//       residual r lies within the truncation band.
+//       residual r lies within kHarvestBand truncation distances (wider than the
+//       band itself, so that the heavy errors of poor pixels - near depth edges,
+//       at grazing angles - are part of what the network learns).
 //   mlp_grad_kernel: one warp per sample, lane j = hidden unit j: forward, the
 //       Gaussian NLL (out + s exp(-out)) / 2 and its backward pass, gradients
 //       summed in registers, then shared memory, then one atomic per parameter
@@ -35,6 +37,8 @@
 
 namespace tsdf {
 namespace {
+
+constexpr float kHarvestBand = 4.0f;   // residuals kept: |r| <= kHarvestBand * delta
 
 __global__ void __launch_bounds__(128) variance_mlp_kernel(const float* __restrict__ depth, FrameParams p,
                                                            const __nv_bfloat16* __restrict__ w,
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(256) harvest_kernel(const float* __restrict__ 
                 const float r = d - dh;
                 const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
                 const float pq = __fmul_rn(sg, sg);
-                take = fabsf(r) <= p.delta && pq > 0.0f;
+                take = fabsf(r) <= kHarvestBand * p.delta && pq > 0.0f;
                 sv = r * r / pq;
             }
         }

@@ -100,9 +100,11 @@ __device__ __forceinline__ float mlp_eval(const MlpShared& m, const float f[kIn]
     return out;
 }
 
-// p_k of pixel (u, v) under the network: p_quad exp(out), or p_quad when
-// |out| > ln 4 or out is not finite; 0 (no measurement) when the pixel's depth
-// is not a valid measurement.
+// p_k of pixel (u, v) under the network: p_quad exp(out), or p_quad when out
+// lies outside [-ln 4, ln 64] or is not finite (a measurement may be up to 64
+// times noisier than the quadratic model says - a sensor far poorer at depth
+// edges - or 4 times less noisy); 0 (no measurement) when the pixel's depth is
+// not a valid measurement.
 __device__ __forceinline__ float learned_variance(const MlpShared& m, const float* __restrict__ depth,
                                                   const FrameParams& p, int u, int v) {
     float f[kIn];
@@ -111,7 +113,7 @@ __device__ __forceinline__ float learned_variance(const MlpShared& m, const floa
     const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
     const float pq = __fmul_rn(sg, sg);
     const float out = mlp_eval(m, f);
-    return (isfinite(out) && fabsf(out) <= 1.3862943611198906f) ? pq * expf(out) : pq;
+    return (out >= -1.3862943611198906f && out <= 4.1588830833596715f) ? pq * expf(out) : pq;   // false for NaN
 }
 
 }  // namespace tsdf

@@ -7,8 +7,9 @@ calls, draws minibatch indices and keeps the buffers (torch tensors).
 Training data: for each frame k of a training sequence, the model fused from
 frames 0..k-1 (quadratic variances) is raycast at pose k; the residual between
 the measured depth and that prediction, at pixels where both exist and the
-residual lies within the truncation band, is a sample of the measurement error
-the variance should describe. The network minimises the Gaussian negative
+residual lies within 4 truncation distances (wider than the band, so that the
+heavy errors of poor pixels are seen), is a sample of the measurement error the
+variance should describe. The network minimises the Gaussian negative
 log-likelihood (out + s exp(-out)) / 2, s = r^2 / p_quad, i.e. it learns
 log(E[r^2] / p_quad) as a function of the pixel's neighbourhood.
 """
@@ -25,6 +26,7 @@ from . import tsdf
 
 N_PARAMS = 1985
 LOG4 = float(np.log(4.0))
+LOG64 = float(np.log(64.0))     # the network's output is used within [-LOG4, LOG64]
 
 
 def _p(t: Optional[torch.Tensor]):

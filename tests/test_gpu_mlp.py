@@ -187,3 +187,28 @@ def test_training_lowers_loss_and_surface_error():
     assert trained < 0.9 * untrained
     assert e_mlp["mae"] < 0.95 * e_quad["mae"] and e_mlp["rms"] < e_quad["rms"]
     assert abs(e_mlp["hits"] - e_quad["hits"]) < 0.01 * e_quad["hits"]
+
+
+def test_training_lowers_surface_error_on_the_edge_noise_sensor():
+    """The sensor the network exists for: deviation 5 times the quadratic one
+    in the edge band and up to 3 times at grazing incidence (the paper's
+    Introduction: edge data are noisier). The room at 640x480 on a 2048^3 grid
+    of 1.5 mm voxels: trained on seeds 100-103 (40 frames each), the network
+    fuses the held-out scene (seed 1, 60 frames) closer to the analytic surface
+    than the quadratic model: residuals up to 4 delta in the training data and
+    outputs up to ln 64 let it give the edge pixels the large variances they
+    need."""
+    sensor = dict(edge_gain=4.0, angle_gain=2.0)
+    train = [synth.room_sequence(seed=sd, n_frames=40, device="cuda", **sensor) for sd in (100, 101, 102, 103)]
+    data = lv.harvest(train, max_n=2_000_000, frame_stride=2)
+    del train
+    assert data.n > 1_000_000, data.n
+    bits, hist = lv.train(data, steps=1500, batch=4096, lr=2e-3, seed=0)
+    ev = synth.room_sequence(seed=1, n_frames=60, device="cuda", **sensor)
+    poses = [ev.poses[k] for k in (10, 25, 40, 55)]
+    e_quad = _fused_error(ev, None, poses)
+    e_mlp = _fused_error(ev, bits, poses)
+    print(f"edge-noise sensor, samples={data.n} loss {hist[0][1]:.4f} -> {hist[-1][1]:.4f}; surface error "
+          f"quadratic {json.dumps(e_quad)} learned {json.dumps(e_mlp)}")
+    assert e_mlp["mae"] < 0.95 * e_quad["mae"] and e_mlp["rms"] < e_quad["rms"]
+    assert abs(e_mlp["hits"] - e_quad["hits"]) < 0.01 * e_quad["hits"]
