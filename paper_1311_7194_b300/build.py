@@ -31,6 +31,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # they are inlined. Host code (pose preparation) is plain IEEE double.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", INCLUDE, "-I", CSRC]
+# The raycast has no bit-exact contract with the oracle (its bar is 0.1 voxel),
+# and its two kernels share every expression, so the compiler may fuse its
+# multiply-adds: measured 1 % faster, results of the two kernels still equal.
+PER_FILE_FLAGS = {"tsdf_raycast.cu": {"-fmad=false": "-fmad=true"}}
 
 
 def nvcc() -> str:
@@ -66,7 +70,8 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
 
     def compile_one(src):
         obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        f = [PER_FILE_FLAGS.get(src, {}).get(x, x) for x in flags]
+        cmd = [cc, *ARCH, *f, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
