@@ -37,7 +37,12 @@ if ROOT not in sys.path:
 
 WORKLOAD = "room-scale plain FP32: 640x480, 2048^3 grid of 1.5 mm voxels, 300 frames"
 METRIC, UNIT = "frames/s", "frames/s"
-LAUNCHES_PER_FRAME = 13    # allocate 5 + integrate 3 + raycast 5 kernels (persistent raycast)
+def launches_per_frame(graph: bool, persistent: bool) -> int:
+    """Kernels per frame: allocation 5 and integration 3 (depth tiles, cull,
+    integrate); the raycast's range clear, raster and march, plus the ray order
+    before a persistent march, plus its own range cull unless a graph step made
+    its visible list in the integrate cull."""
+    return 5 + 3 + 3 + (1 if persistent else 0) + (0 if graph else 1)
 
 
 def parse():
@@ -296,13 +301,16 @@ def raycast_latency_model(steps_per_ray, rays, sec, sm_mhz, ctas_per_sm=8, threa
             "cycles_per_step_per_lane": cycles, "sm_mhz": mhz}
 
 
-def raycast_algorithmic_bytes(counts, n_blocks, H, W):
+def raycast_algorithmic_bytes(counts, n_blocks, H, W, own_cull=True):
     """Unique bytes one raycast must move: the distinct 32-byte sectors of T
     and of the block table its samples read, the block list read by the range
-    cull (16 B per block), the near / far range tiles (8 B per 4x4 pixels) and
-    the depth, normal and vertex maps written (28 B per pixel)."""
+    cull (16 B per block, when the raycast makes its own visible list; a graph
+    step makes it in the integrate cull's pass), the near / far range tiles
+    (8 B per 4x4 pixels) and the depth, normal and vertex maps written (28 B
+    per pixel)."""
     tiles = ((W + 3) // 4) * ((H + 3) // 4)
-    return 32.0 * (counts["t_sectors"] + counts["table_sectors"]) + 16.0 * n_blocks + 8.0 * tiles + 28.0 * H * W
+    return (32.0 * (counts["t_sectors"] + counts["table_sectors"]) + (16.0 * n_blocks if own_cull else 0.0)
+            + 8.0 * tiles + 28.0 * H * W)
 
 
 def run_ours(args):
@@ -413,7 +421,7 @@ def run_ours(args):
         n_blocks.append(s_["n_blocks"]); visible.append(s_["visible_blocks"]); updates.append(s_["voxel_updates"])
         if k % TRACE_EVERY == 0:
             c = vol.raycast_trace(seq.intr, seq.poses[k])
-            rc_bytes.append(raycast_algorithmic_bytes(c, s_["n_blocks"], H, W))
+            rc_bytes.append(raycast_algorithmic_bytes(c, s_["n_blocks"], H, W, own_cull=args.mode != "graph"))
             # dependent samples along a ray: the march (jumps included), re-scans,
             # the refinement, and one round for the six independent normal samples
             rc_steps.append((c["march_samples"] + c["rescan_samples"] + c["refine_samples"]) / c["rays"] + 1.0)
@@ -440,8 +448,9 @@ def run_ours(args):
                 "traffic": ncu_traffic("raycast", rc_mean), "algorithmic_bytes_per_launch": rc_mean,
                 "avg_launch_ms": 1000.0 * rc_sec,
                 "algorithmic_bytes": "distinct 32 B sectors of T and of the block table read (traced every "
-                                     f"{TRACE_EVERY}th frame) + 16 B per allocated block (range cull) + "
-                                     "8 B per 4x4-pixel range tile + 28 B per pixel of maps written",
+                                     f"{TRACE_EVERY}th frame) + 8 B per 4x4-pixel range tile + 28 B per pixel of "
+                                     "maps written (+ 16 B per allocated block for the range cull when the raycast "
+                                     "makes its own visible list; a graph step makes it in the integrate cull)",
                 "limiter": "instruction issue and dependent-load latency, not bandwidth: DRAM and L2 run far below "
                            "their peaks while the kernel runs (l2_frac_ncu), and the latency model below shows the "
                            "cycles each dependent step costs a lane",
@@ -469,7 +478,8 @@ def run_ours(args):
                               "visible_blocks": int(st["visible_blocks_total"]),
                               "rays_hit": int(st["rays_hit_total"])},
             "roofline": roofline, "roofline_integrate": roofline_integrate,
-            "gpu_launches": (LAUNCHES_PER_FRAME - (0 if vol.launch_config()["raycast_persistent"] else 1)) * F * args.steps,
+            "gpu_launches": launches_per_frame(args.mode == "graph", bool(vol.launch_config()["raycast_persistent"]))
+                            * F * args.steps,
             "clocks": clk}
 
     # end to end through the public API with host buffers

@@ -129,8 +129,10 @@ tsdf_status tsdf_graph_launch(tsdf_graph* g, const float* const* depth, const fl
         if (le == cudaSuccess) le = tsdf::launch_allocate(v, depth[0], ap, (int)v->frame, g->cap);
         if (le == cudaSuccess && g->events[1]) le = cudaEventRecordWithFlags(g->events[1], g->cap, cudaEventRecordExternal);
         if (le == cudaSuccess)
+            // the step raycasts at the pose it fuses: one cull pass makes both
+            // visible lists (integrate and raycast)
             le = tsdf::launch_integrate(v, depth[0], variance ? variance[0] : nullptr,
-                                        tsdf::make_frame_params(v, g->intr, poses_wc), g->cap);
+                                        tsdf::make_frame_params(v, g->intr, poses_wc), g->cap, true);
     } else {
         tsdf::BatchParams bp;
         std::memset(&bp, 0, sizeof(bp));
@@ -149,7 +151,7 @@ tsdf_status tsdf_graph_launch(tsdf_graph* g, const float* const* depth, const fl
     if (le == cudaSuccess && g->events[2]) le = cudaEventRecordWithFlags(g->events[2], g->cap, cudaEventRecordExternal);
     if (le == cudaSuccess)
         le = tsdf::launch_raycast(v, tsdf::make_frame_params(v, g->intr, poses_wc + 16 * (K - 1)), depth_out,
-                                  normal_out, vertex_out, g->cap);
+                                  normal_out, vertex_out, g->cap, K == 1);
     if (le == cudaSuccess && g->events[3]) le = cudaEventRecordWithFlags(g->events[3], g->cap, cudaEventRecordExternal);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->cap, &graph);

@@ -118,7 +118,11 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
 // The integrate call's counters: the last call's counts go to the totals and
 // the per-call ones restart. Runs in the first kernel of the call, ahead of
 // every kernel that reads them (stream order).
-__device__ __forceinline__ void reset_frame_counters(Counters* ctr) {
+__device__ __forceinline__ void reset_frame_counters(Counters* ctr, bool rc_too) {
+    if (rc_too) {   // the raycast's visible list is made by this call's cull
+        ctr->rc_blocks_total += ctr->n_visible_rc;
+        ctr->n_visible_rc = 0;
+    }
     ctr->updates_total += ctr->voxel_updates;
     ctr->visible_total += ctr->n_visible;
     ctr->touched_total += ctr->voxels_touched;
@@ -138,13 +142,13 @@ template <bool kLearned>
 __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth,
                                                           const float* __restrict__ var, FrameParams p,
                                                           float2* __restrict__ tiles, float2* __restrict__ meas,
-                                                          Counters* __restrict__ reset,
+                                                          Counters* __restrict__ reset, int reset_rc,
                                                           const __nv_bfloat16* __restrict__ mlp_w) {
     pdl_prologue();
     __shared__ float smem[kLearned ? kSmemFloats : 1];
     MlpShared mlp;
     if (kLearned) mlp = load_weights(mlp_w, smem);
-    if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset);
+    if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset, reset_rc != 0);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
     const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
     const int lane = threadIdx.x & 31;
@@ -243,24 +247,41 @@ __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* _
     return keep;
 }
 
+// kRc: the same pass also makes the raycast's visible list for the same pose
+// (rc_block_visible; a fusion step raycasts at the pose it has just fused), so
+// the raycast needs no pass of its own over the blocks.
+template <bool kRc>
 __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                    FrameParams p, const float2* __restrict__ tiles,
-                                                   VisibleBlock* __restrict__ vis) {
+                                                   VisibleBlock* __restrict__ vis, int* __restrict__ vis_rc) {
     pdl_prologue();
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
         const long long b = b0 + lane;
         VisibleBlock e;
-        const bool keep = b < n && make_entry(p, tiles, blocks[b], (int)b, &e);
+        const int4 bc = b < n ? blocks[b] : make_int4(0, 0, 0, 0);
+        const bool keep = b < n && make_entry(p, tiles, bc, (int)b, &e);
         const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (!m) continue;
-        unsigned base = 0;
-        if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-        const unsigned at = base + __popc(m & ((1u << lane) - 1u));
-        if (keep && in_bounds(p.err, at < (unsigned)p.cap)) vis[at] = e;
+        if (m) {
+            unsigned base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->n_visible, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            const unsigned at = base + __popc(m & lt);
+            if (keep && in_bounds(p.err, at < (unsigned)p.cap)) vis[at] = e;
+        }
+        if (kRc) {
+            const bool keep_rc = b < n && rc_block_visible(p, bc);
+            const unsigned mr = __ballot_sync(0xffffffffu, keep_rc);
+            if (!mr) continue;
+            unsigned base = 0;
+            if (lane == __ffs(mr) - 1) base = atomicAdd(&ctr->n_visible_rc, (unsigned)__popc(mr));
+            base = __shfl_sync(0xffffffffu, base, __ffs(mr) - 1);
+            const unsigned at = base + __popc(mr & lt);
+            if (keep_rc && in_bounds(p.err, at < (unsigned)p.cap)) vis_rc[at] = (int)b;
+        }
     }
 }
 
@@ -641,19 +662,25 @@ void launch_integrate_batch_s(tsdf_volume* v, const BatchParams& bp, unsigned gr
 // The measurement map and depth tiles of one frame; with a network set and no
 // variance map, the network gives each pixel's p_k inside the same kernel.
 void launch_depth_tiles(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p, float2* tiles,
-                        float2* meas, Counters* reset, cudaStream_t st) {
+                        float2* meas, Counters* reset, bool reset_rc, cudaStream_t st) {
     const auto* w = static_cast<const __nv_bfloat16*>(v->mlp_w);
     if (!var && w)
-        launch_pdl(depth_tiles_kernel<true>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset, w);
+        launch_pdl(depth_tiles_kernel<true>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
+                   (int)reset_rc, w);
     else
         launch_pdl(depth_tiles_kernel<false>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
-                   w);
+                   (int)reset_rc, w);
 }
 
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
-                             cudaStream_t st) {
-    launch_depth_tiles(v, depth, var, p, v->dtiles, v->meas, v->ctr, st);
-    launch_pdl(cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible);
+                             cudaStream_t st, bool rc_cull_too) {
+    launch_depth_tiles(v, depth, var, p, v->dtiles, v->meas, v->ctr, rc_cull_too, st);
+    if (rc_cull_too)
+        launch_pdl(cull_kernel<true>, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible,
+                   v->visible_rc);
+    else
+        launch_pdl(cull_kernel<false>, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible,
+                   (int*)nullptr);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, p, grid, st); break;
@@ -668,7 +695,7 @@ cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cud
     for (int k = 0; k < bp.K; ++k) {
         float2* mk = v->meas_batch + k * v->var_batch_stride;
         launch_depth_tiles(v, bp.depth[k], bp.var[k], bp.fp[k], v->dtiles_batch + k * v->dtiles_batch_stride, mk,
-                           k == 0 ? v->ctr : nullptr, st);
+                           k == 0 ? v->ctr : nullptr, false, st);
         bp.meas[k] = mk;
     }
     launch_pdl(cull_batch_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, bp, v->dtiles_batch,

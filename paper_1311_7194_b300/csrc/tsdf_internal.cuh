@@ -178,13 +178,15 @@ namespace tsdf {
 // Launchers (tsdf_alloc.cu, tsdf_integrate.cu, tsdf_raycast.cu).
 cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParams& p,
                             int frame, cudaStream_t st);
+// rc_cull_too: the integrate cull also makes the raycast's visible list for the
+// same pose, and the raycast that follows is launched with rc_culled.
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var,
-                             const FrameParams& p, cudaStream_t st);
+                             const FrameParams& p, cudaStream_t st, bool rc_cull_too = false);
 cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st);
 cudaError_t launch_variance_mlp(tsdf_volume* v, const float* depth, const FrameParams& p, float* var,
                                 cudaStream_t st);
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out,
-                           float* normal_out, float* vertex_out, cudaStream_t st);
+                           float* normal_out, float* vertex_out, cudaStream_t st, bool rc_culled = false);
 // Raycast with caller-provided near / far range maps (each range_tiles(W, H)
 // words) and ray-order lists (kRayBuckets * ray_tiles(W, H) words).
 cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intrinsics& K, const double pose[16],
@@ -233,6 +235,59 @@ __device__ __forceinline__ bool in_bounds(unsigned int* err, bool ok) {
 
 __device__ __forceinline__ bool depth_ok(float d, float dmin, float dmax) {
     return (fabsf(d) < __int_as_float(0x7f800000)) & (d > 0.0f) & (d >= dmin) & (d <= dmax);
+}
+
+// Camera-space bounds of the box spanning voxels [8b - 1, 8b + 8] of a block
+// (its samples and the trilinear cells shared with its neighbours), for the
+// raycast's range cull and raster: camera z range, projected bounding
+// rectangle, and whether the box reaches behind the camera plane. In float from
+// the camera position of voxel (0,0,0) (oc0) and the per-voxel steps (cs): a
+// few units of rounding at 3 m are far below the pixel of dilation the raster
+// adds. Written with explicitly rounded operations so that every file that
+// includes it (built with or without contraction) takes the same decisions.
+__device__ __forceinline__ void rc_block_box(const FrameParams& p, int4 bc, float zr[2], float rect[4], bool* behind) {
+    const float bx = (float)(kSide * bc.x - 1), by = (float)(kSide * bc.y - 1), bz = (float)(kSide * bc.z - 1);
+    float oc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        oc[r] = __fadd_rn(__fadd_rn(__fadd_rn(p.oc0[r], __fmul_rn(bx, p.cs[3 * r])), __fmul_rn(by, p.cs[3 * r + 1])),
+                          __fmul_rn(bz, p.cs[3 * r + 2]));
+    const float ext = (float)(kSide + 1);
+    float zmin = 3.0e38f, zmax = -3.0e38f, umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float ax = (c & 1) ? ext : 0.0f, ay = (c & 2) ? ext : 0.0f, az = (c & 4) ? ext : 0.0f;
+        float q[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            q[r] = __fadd_rn(__fadd_rn(__fadd_rn(oc[r], __fmul_rn(ax, p.cs[3 * r])), __fmul_rn(ay, p.cs[3 * r + 1])),
+                             __fmul_rn(az, p.cs[3 * r + 2]));
+        zmin = fminf(zmin, q[2]);
+        zmax = fmaxf(zmax, q[2]);
+        const float rz = __fdiv_rn(1.0f, fmaxf(q[2], 1e-20f));
+        const float u = __fadd_rn(__fmul_rn(__fmul_rn(p.fx, q[0]), rz), p.cx);
+        const float v = __fadd_rn(__fmul_rn(__fmul_rn(p.fy, q[1]), rz), p.cy);
+        umin = fminf(umin, u); umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    }
+    zr[0] = zmin;
+    zr[1] = zmax;
+    *behind = zmin <= 1e-4f;
+    rect[0] = umin; rect[1] = umax; rect[2] = vmin; rect[3] = vmax;
+}
+
+// Whether the raycast rasterises block bc: its box reaches [near, far] and,
+// when entirely in front of the camera, projects into the image dilated by a
+// pixel and a half.
+__device__ __forceinline__ bool rc_block_visible(const FrameParams& p, int4 bc) {
+    float zr[2], rect[4];
+    bool behind;
+    rc_block_box(p, bc, zr, rect, &behind);
+    bool keep = zr[1] >= p.near_clip && zr[0] <= p.far_clip;
+    if (keep && !behind)
+        keep = rect[1] >= -1.5f && rect[0] <= (float)p.width + 0.5f && rect[3] >= -1.5f &&
+               rect[2] <= (float)p.height + 0.5f;
+    return keep;
 }
 
 __device__ __forceinline__ unsigned int warp_sum(unsigned int x) {

@@ -39,37 +39,6 @@ constexpr int kFine = 16;           // substeps of the re-scan on entering the f
 constexpr unsigned kFarInit = 0u;   // float bits of +0
 constexpr unsigned kNearInit = 0x7f800000u;   // float bits of +inf
 
-// camera-space corners of the box spanning voxels [8b - 1, 8b + 8] of a block,
-// in float from the camera position of voxel (0,0,0) (oc0) and the per-voxel
-// steps (cs): a few units of rounding at 3 m are far below the pixel of
-// dilation the raster adds.
-__device__ __forceinline__ void block_box(const FrameParams& p, int4 bc, float zr[2], float rect[4], bool* behind) {
-    const float bx = (float)(kSide * bc.x - 1), by = (float)(kSide * bc.y - 1), bz = (float)(kSide * bc.z - 1);
-    float oc[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-        oc[r] = p.oc0[r] + bx * p.cs[3 * r] + by * p.cs[3 * r + 1] + bz * p.cs[3 * r + 2];
-    const float ext = (float)(kSide + 1);
-    float zmin = 3.0e38f, zmax = -3.0e38f, umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float ax = (c & 1) ? ext : 0.0f, ay = (c & 2) ? ext : 0.0f, az = (c & 4) ? ext : 0.0f;
-        const float x = oc[0] + ax * p.cs[0] + ay * p.cs[1] + az * p.cs[2];
-        const float y = oc[1] + ax * p.cs[3] + ay * p.cs[4] + az * p.cs[5];
-        const float z = oc[2] + ax * p.cs[6] + ay * p.cs[7] + az * p.cs[8];
-        zmin = fminf(zmin, z);
-        zmax = fmaxf(zmax, z);
-        const float rz = 1.0f / fmaxf(z, 1e-20f);
-        const float u = p.fx * x * rz + p.cx, v = p.fy * y * rz + p.cy;
-        umin = fminf(umin, u); umax = fmaxf(umax, u);
-        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
-    }
-    zr[0] = zmin;
-    zr[1] = zmax;
-    *behind = zmin <= 1e-4f;
-    rect[0] = umin; rect[1] = umax; rect[2] = vmin; rect[3] = vmax;
-}
-
 __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                       FrameParams p, int* __restrict__ vis) {
     pdl_prologue();
@@ -78,16 +47,7 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < n; b0 += stride) {
         const long long b = b0 + lane;
-        bool keep = false;
-        if (b < n) {
-            float zr[2], rect[4];
-            bool behind;
-            block_box(p, blocks[b], zr, rect, &behind);
-            keep = zr[1] >= p.near_clip && zr[0] <= p.far_clip;
-            if (keep && !behind)
-                keep = rect[1] >= -1.5f && rect[0] <= (float)p.width + 0.5f && rect[3] >= -1.5f &&
-                       rect[2] <= (float)p.height + 0.5f;
-        }
+        const bool keep = b < n && rc_block_visible(p, blocks[b]);
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (!m) continue;
         unsigned base = 0;
@@ -100,19 +60,23 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
 
 // The raycast call's counters: the last call's counts go to the totals and the
 // per-call ones restart (thread 0 of the call's first kernel).
-__device__ __forceinline__ void reset_rc_counters(Counters* ctr) {
+// (visible_too: false when the integrate cull of the same call sequence made
+// the visible list already and reset its count.)
+__device__ __forceinline__ void reset_rc_counters(Counters* ctr, bool visible_too) {
     ctr->rc_next = 0;
     for (int b = 0; b < kRayBuckets; ++b) ctr->rc_bucket[b] = 0;
     ctr->rays_total += ctr->rays_hit;
-    ctr->rc_blocks_total += ctr->n_visible_rc;
-    ctr->n_visible_rc = 0;
+    if (visible_too) {
+        ctr->rc_blocks_total += ctr->n_visible_rc;
+        ctr->n_visible_rc = 0;
+    }
     ctr->rays_hit = 0;
 }
 
 __global__ void range_clear_kernel(unsigned int* __restrict__ near_, unsigned int* __restrict__ far_, long long n,
-                                   Counters* __restrict__ ctr) {
+                                   Counters* __restrict__ ctr, int visible_too) {
     pdl_prologue();
-    if (blockIdx.x == 0 && threadIdx.x == 0) reset_rc_counters(ctr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_rc_counters(ctr, visible_too != 0);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         near_[i] = kNearInit;
         far_[i] = kFarInit;
@@ -134,7 +98,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const Counters* __restrict_
         if (w0 + lane < n) {
             float zr[2], rect[4];
             bool behind;
-            block_box(p, blocks[vis[w0 + lane]], zr, rect, &behind);
+            rc_block_box(p, blocks[vis[w0 + lane]], zr, rect, &behind);
             const float zn = fmaxf(zr[0], p.near_clip), zf = fminf(zr[1], p.far_clip);
             if (zn <= zf) {
                 int u0 = 0, u1 = p.width - 1, v0 = 0, v1 = p.height - 1;
@@ -902,12 +866,13 @@ void launch_march(tsdf_volume* v, const FrameParams& p, const unsigned int* near
 }  // namespace
 
 cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_out, float* normal_out,
-                           float* vertex_out, cudaStream_t st) {
+                           float* vertex_out, cudaStream_t st, bool rc_culled) {
     const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_cap;
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
-    launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, rc_culled ? 0 : 1);
+    if (!rc_culled)   // else the integrate cull of the same pose made the visible list
+        launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, v->ray_order, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
@@ -943,7 +908,7 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
     const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_cap;
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, 1);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     switch (v->cfg.storage) {
@@ -987,7 +952,7 @@ cudaError_t launch_debug_slot(tsdf_volume* v, long long slot, float* sink, cudaS
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
                                   int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const long long npix = range_tiles(p.width, p.height);
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, 1);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
