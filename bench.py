@@ -38,11 +38,11 @@ if ROOT not in sys.path:
 WORKLOAD = "room-scale plain FP32: 640x480, 2048^3 grid of 1.5 mm voxels, 300 frames"
 METRIC, UNIT = "frames/s", "frames/s"
 def launches_per_frame(graph: bool, persistent: bool) -> int:
-    """Kernels per frame: allocation 5 and integration 3 (depth tiles, cull,
-    integrate); the raycast's range clear, raster and march, plus the ray order
-    before a persistent march, plus its own range cull unless a graph step made
-    its visible list in the integrate cull."""
-    return 5 + 3 + 3 + (1 if persistent else 0) + (0 if graph else 1)
+    """Kernels per frame: allocation 5 (mark, count, assign, commit, chi fill)
+    and integration 3 (depth tiles, cull, integrate); the raycast's raster and
+    march, plus the ray order before a persistent march, plus its own range
+    clear and range cull unless a graph step's integrate cull did both."""
+    return 5 + 3 + 2 + (1 if persistent else 0) + (0 if graph else 2)
 
 
 def parse():

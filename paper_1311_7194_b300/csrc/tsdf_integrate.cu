@@ -119,10 +119,7 @@ __device__ __forceinline__ bool box_visible(const FrameParams& p, const float oc
 // the per-call ones restart. Runs in the first kernel of the call, ahead of
 // every kernel that reads them (stream order).
 __device__ __forceinline__ void reset_frame_counters(Counters* ctr, bool rc_too) {
-    if (rc_too) {   // the raycast's visible list is made by this call's cull
-        ctr->rc_blocks_total += ctr->n_visible_rc;
-        ctr->n_visible_rc = 0;
-    }
+    if (rc_too) reset_raycast_counters(ctr);   // this stage also starts the step's raycast
     ctr->updates_total += ctr->voxel_updates;
     ctr->visible_total += ctr->n_visible;
     ctr->touched_total += ctr->voxels_touched;
@@ -247,14 +244,23 @@ __device__ __forceinline__ bool make_entry(const FrameParams& p, const float2* _
     return keep;
 }
 
-// kRc: the same pass also makes the raycast's visible list for the same pose
-// (rc_block_visible; a fusion step raycasts at the pose it has just fused), so
-// the raycast needs no pass of its own over the blocks.
+// kRc: the same pass also starts the raycast of the same pose (a fusion step
+// raycasts at the pose it has just fused): it clears the range maps and makes
+// the raycast's visible list (rc_block_visible), so the raycast needs no pass
+// of its own over the blocks.
 template <bool kRc>
 __global__ void __launch_bounds__(256) cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                    FrameParams p, const float2* __restrict__ tiles,
-                                                   VisibleBlock* __restrict__ vis, int* __restrict__ vis_rc) {
+                                                   VisibleBlock* __restrict__ vis, int* __restrict__ vis_rc,
+                                                   unsigned int* __restrict__ near_, unsigned int* __restrict__ far_,
+                                                   long long n_range) {
     pdl_prologue();
+    if (kRc)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_range;
+             i += (long long)gridDim.x * blockDim.x) {
+            near_[i] = kNearInit;
+            far_[i] = kFarInit;
+        }
     const long long n = ctr->n_blocks;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -677,10 +683,10 @@ cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* va
     launch_depth_tiles(v, depth, var, p, v->dtiles, v->meas, v->ctr, rc_cull_too, st);
     if (rc_cull_too)
         launch_pdl(cull_kernel<true>, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible,
-                   v->visible_rc);
+                   v->visible_rc, v->range, v->range + v->range_cap, (long long)range_tiles(p.width, p.height));
     else
         launch_pdl(cull_kernel<false>, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->dtiles, v->visible,
-                   (int*)nullptr);
+                   (int*)nullptr, (unsigned int*)nullptr, (unsigned int*)nullptr, 0ll);
     const unsigned grid = (unsigned)(v->num_sms * v->lc.integrate_ctas_per_sm);
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_s<TSDF_STORAGE_F16>(v, depth, p, grid, st); break;

@@ -21,6 +21,8 @@ constexpr int kMaxBatch = 8;             // frames per tsdf_integrate_batch call
 constexpr int kMlpParams = 1985;         // learned-variance network: 27-32-32-1
 constexpr int kOcc2 = 4;                 // occupancy level 2: cells of 4^3 blocks (32 voxels a side)
 constexpr int kRangeTile = 4;            // raycast range maps hold one near / far pair per 4x4 pixels
+constexpr unsigned kFarInit = 0u;        // range maps' initial values: float bits of +0 (far)
+constexpr unsigned kNearInit = 0x7f800000u;   // and of +inf (near)
 
 // Entries of one raycast range map (near or far) for a width x height image.
 inline int64_t range_tiles(int width, int height) {
@@ -178,8 +180,9 @@ namespace tsdf {
 // Launchers (tsdf_alloc.cu, tsdf_integrate.cu, tsdf_raycast.cu).
 cudaError_t launch_allocate(tsdf_volume* v, const float* depth, const AllocParams& p,
                             int frame, cudaStream_t st);
-// rc_cull_too: the integrate cull also makes the raycast's visible list for the
-// same pose, and the raycast that follows is launched with rc_culled.
+// rc_cull_too: the integrate stage also starts the raycast of the same pose
+// (counters, range maps cleared, visible list), and the raycast that follows
+// is launched with rc_culled.
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var,
                              const FrameParams& p, cudaStream_t st, bool rc_cull_too = false);
 cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp, cudaStream_t st);
@@ -288,6 +291,19 @@ __device__ __forceinline__ bool rc_block_visible(const FrameParams& p, int4 bc) 
         keep = rect[1] >= -1.5f && rect[0] <= (float)p.width + 0.5f && rect[3] >= -1.5f &&
                rect[2] <= (float)p.height + 0.5f;
     return keep;
+}
+
+// The raycast call's counters: the last call's counts go to the totals and the
+// per-call ones restart. Run by one thread of the first kernel of the call
+// (the range clear, or in a graph step the integrate stage's first kernel,
+// whose cull also makes the raycast's visible list).
+__device__ __forceinline__ void reset_raycast_counters(Counters* ctr) {
+    ctr->rc_next = 0;
+    for (int b = 0; b < kRayBuckets; ++b) ctr->rc_bucket[b] = 0;
+    ctr->rays_total += ctr->rays_hit;
+    ctr->rays_hit = 0;
+    ctr->rc_blocks_total += ctr->n_visible_rc;
+    ctr->n_visible_rc = 0;
 }
 
 __device__ __forceinline__ unsigned int warp_sum(unsigned int x) {

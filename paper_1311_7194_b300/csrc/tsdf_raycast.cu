@@ -36,8 +36,6 @@ namespace {
 constexpr int kMaxMarch = 8192;     // bound on march iterations per ray
 constexpr int kRefine = 10;         // refinement samples per hit (Illinois false position)
 constexpr int kFine = 16;           // substeps of the re-scan on entering the field below zero
-constexpr unsigned kFarInit = 0u;   // float bits of +0
-constexpr unsigned kNearInit = 0x7f800000u;   // float bits of +inf
 
 __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr, const int4* __restrict__ blocks,
                                                       FrameParams p, int* __restrict__ vis) {
@@ -58,25 +56,10 @@ __global__ void __launch_bounds__(256) rc_cull_kernel(Counters* __restrict__ ctr
     }
 }
 
-// The raycast call's counters: the last call's counts go to the totals and the
-// per-call ones restart (thread 0 of the call's first kernel).
-// (visible_too: false when the integrate cull of the same call sequence made
-// the visible list already and reset its count.)
-__device__ __forceinline__ void reset_rc_counters(Counters* ctr, bool visible_too) {
-    ctr->rc_next = 0;
-    for (int b = 0; b < kRayBuckets; ++b) ctr->rc_bucket[b] = 0;
-    ctr->rays_total += ctr->rays_hit;
-    if (visible_too) {
-        ctr->rc_blocks_total += ctr->n_visible_rc;
-        ctr->n_visible_rc = 0;
-    }
-    ctr->rays_hit = 0;
-}
-
 __global__ void range_clear_kernel(unsigned int* __restrict__ near_, unsigned int* __restrict__ far_, long long n,
-                                   Counters* __restrict__ ctr, int visible_too) {
+                                   Counters* __restrict__ ctr) {
     pdl_prologue();
-    if (blockIdx.x == 0 && threadIdx.x == 0) reset_rc_counters(ctr, visible_too != 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_raycast_counters(ctr);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         near_[i] = kNearInit;
         far_[i] = kFarInit;
@@ -870,9 +853,10 @@ cudaError_t launch_raycast(tsdf_volume* v, const FrameParams& p, float* depth_ou
     const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_cap;
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, rc_culled ? 0 : 1);
-    if (!rc_culled)   // else the integrate cull of the same pose made the visible list
+    if (!rc_culled) {   // else the integrate stage of the same pose cleared the maps and made the visible list
+        launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
         launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
+    }
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, v->ray_order, depth_out, normal_out, vertex_out, st);
     return cudaGetLastError();
@@ -908,7 +892,7 @@ cudaError_t launch_raycast_trace(tsdf_volume* v, const FrameParams& p, unsigned 
     const long long npix = range_tiles(p.width, p.height);
     unsigned int* near_ = v->range;
     unsigned int* far_ = v->range + v->range_cap;
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, 1);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     switch (v->cfg.storage) {
@@ -952,7 +936,7 @@ cudaError_t launch_debug_slot(tsdf_volume* v, long long slot, float* sink, cudaS
 cudaError_t launch_raycast_ranges(tsdf_volume* v, const FrameParams& p, unsigned int* near_, unsigned int* far_,
                                   int* order, float* depth_out, float* normal_out, float* vertex_out, cudaStream_t st) {
     const long long npix = range_tiles(p.width, p.height);
-    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr, 1);
+    launch_pdl(range_clear_kernel, dim3(v->num_sms * 4), dim3(256), st, near_, far_, npix, v->ctr);
     launch_pdl(rc_cull_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, p, v->visible_rc);
     launch_pdl(raster_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->visible_rc, v->blocks, p, near_, far_);
     launch_march(v, p, near_, far_, order, depth_out, normal_out, vertex_out, st);
