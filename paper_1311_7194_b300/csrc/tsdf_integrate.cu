@@ -537,8 +537,12 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
 // before the block's allocation - and stored once. Same measurement and update
 // functions as integrate_kernel, so the result equals K sequential calls bit
 // for bit.
+// The grid is kBatchCtasPerSm CTAs per SM, all resident at once (the launch
+// bounds cap the registers accordingly).
+constexpr int kBatchCtasPerSm = 12;
+
 template <int kS, int kRule, bool kRefine>
-__global__ void __launch_bounds__(kIntegrateThreads) integrate_batch_kernel(Counters* __restrict__ ctr,
+__global__ void __launch_bounds__(kIntegrateThreads, kBatchCtasPerSm) integrate_batch_kernel(Counters* __restrict__ ctr,
                                                                             const VisibleBlock* __restrict__ vis,
                                                                             const int4* __restrict__ blocks,
                                                                             typename Codec<kS>::E* __restrict__ T,
@@ -706,7 +710,7 @@ cudaError_t launch_integrate_batch(tsdf_volume* v, const BatchParams& bp_in, cud
     }
     launch_pdl(cull_batch_kernel, dim3(v->num_sms * 8), dim3(256), st, v->ctr, v->blocks, bp, v->dtiles_batch,
                v->dtiles_batch_stride, v->visible_batch);
-    const unsigned grid = (unsigned)v->num_sms * 12;
+    const unsigned grid = (unsigned)v->num_sms * kBatchCtasPerSm;
     switch (v->cfg.storage) {
         case TSDF_STORAGE_F16: launch_integrate_batch_s<TSDF_STORAGE_F16>(v, bp, grid, st); break;
         case TSDF_STORAGE_SNORM16: launch_integrate_batch_s<TSDF_STORAGE_SNORM16>(v, bp, grid, st); break;
