@@ -58,6 +58,9 @@ def parse():
                     help="skip the other configurations the default line carries (batched K=8, capsules in three "
                          "storage formats, FP16 + batched + learned against plain FP32)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--launch-shape", default=None, metavar="VPT,CTAS,PERSISTENT",
+                    help="room workload: set the launch shape (integrate voxels per thread, integrate CTAs per SM, "
+                         "1 for the persistent raycast) instead of autotuning it")
     ap.add_argument("--block-capacity", type=int, default=None, help="pool size in blocks")
     ap.add_argument("--mode", choices=["graph", "direct"], default="graph",
                     help="graph: each step one CUDA graph launch; direct: one C-ABI call per stage")
@@ -250,13 +253,13 @@ def _sha(path):
 # with the hash of the kernel source it was measured on; a value is dropped
 # when that source changes.
 NCU_TRAFFIC = {
-    # frames 100-109, 10 launches each of depth_tiles + cull + integrate:
-    # 2141.8 MB over 76.55 M voxel updates
-    "integrate": {"sha": "bae62bb20ea903a0", "bytes_per_unit": 27.98},
-    # same frames, 10 launches each of clear + range cull + raster +
-    # persistent raycast: 1016.3 MB against 816.0 MB of traced unique bytes,
-    # i.e. DRAM bytes per algorithmic byte
-    "raycast": {"sha": "68111240e633b1ca", "bytes_per_unit": 1.2454},
+    # frames 100-109, 10 launches each of depth_tiles + cull (which also makes
+    # the raycast's visible list) + integrate: 2144.8 MB over 76.55 M voxel updates
+    "integrate": {"sha": "9d7d503f6ec87abf", "bytes_per_unit": 28.02},
+    # same frames, 10 launches each of raster + ray order + persistent raycast:
+    # 1014.7 MB against 783.8 MB of traced unique bytes, i.e. DRAM bytes per
+    # algorithmic byte
+    "raycast": {"sha": "e3bf95a41e672e86", "bytes_per_unit": 1.2946},
 }
 STAGE_SOURCES = {"integrate": "tsdf_integrate.cu", "raycast": "tsdf_raycast.cu"}
 TRACE_EVERY = 10
@@ -273,7 +276,7 @@ def ncu_traffic(stage, units):
 # L2 throughput of the persistent raycast kernel as a fraction of its peak (ncu
 # "L2 Cache Throughput", one capture of the room workload), with the hash of the
 # kernel source it was measured on; dropped when that source changes.
-NCU_L2 = {"raycast": {"sha": None, "frac": 0.15}}
+NCU_L2 = {"raycast": {"sha": "e3bf95a41e672e86", "frac": 0.133}}
 
 
 def ncu_l2_frac(stage):
@@ -338,7 +341,11 @@ def run_ours(args):
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume)
     tuned = None
-    if not args.no_autotune:
+    if args.launch_shape:
+        vpt, ctas, persistent = (int(x) for x in args.launch_shape.split(","))
+        vol.set_launch_config(integrate_voxels_per_thread=vpt, integrate_ctas_per_sm=ctas,
+                              raycast_persistent=persistent)
+    elif not args.no_autotune:
         # launch shapes picked on the first frames (results do not depend on them)
         n_tune = min(20, F)
         tuned, _ = vol.autotune([depth_dev[k] for k in range(n_tune)], seq.intr, seq.poses[:n_tune],

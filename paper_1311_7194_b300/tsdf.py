@@ -468,7 +468,10 @@ class Volume:
     def set_launch_config(self, **kw):
         c = LaunchConfig()
         _check(self.lib.tsdf_get_launch_config(self.h, ctypes.byref(c)), "tsdf_get_launch_config")
+        names = {f for f, _ in LaunchConfig._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise TypeError(f"set_launch_config: unknown field {k!r} (fields: {sorted(names)})")
             setattr(c, k, int(v))
         _check(self.lib.tsdf_set_launch_config(self.h, ctypes.byref(c)), "tsdf_set_launch_config")
 

@@ -58,6 +58,8 @@ def test_bad_launch_shapes_are_rejected():
                 dict(integrate_ctas_per_sm=33), dict(raycast_tile_w=7), dict(raycast_persistent=2)]:
         with pytest.raises(tsdf.TsdfError):
             vol.set_launch_config(**bad)
+    with pytest.raises(TypeError):
+        vol.set_launch_config(integrate_vpt=8)   # not a field name: rejected, not ignored
     assert vol.launch_config() == dict(integrate_voxels_per_thread=4, integrate_ctas_per_sm=12,
                                        raycast_tile_w=16, raycast_tile_h=8, raycast_persistent=0)
 
