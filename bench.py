@@ -304,6 +304,23 @@ def raycast_latency_model(steps_per_ray, rays, sec, sm_mhz, ctas_per_sm=8, threa
             "cycles_per_step_per_lane": cycles, "sm_mhz": mhz}
 
 
+def choose_launch(vol, args, depth_dev, seq, n_tune=20):
+    """The launch shape of a workload's volume: the one --launch-shape names,
+    else the autotuner's pick on the first frames (it empties the volume;
+    results do not depend on the shape), else the library's default."""
+    if getattr(args, "launch_shape", None):
+        vpt, ctas, persistent = (int(x) for x in args.launch_shape.split(","))
+        vol.set_launch_config(integrate_voxels_per_thread=vpt, integrate_ctas_per_sm=ctas,
+                              raycast_persistent=persistent)
+        return vol.launch_config()
+    if not getattr(args, "no_autotune", False):
+        n = min(n_tune, int(depth_dev.shape[0]))
+        tuned, _ = vol.autotune([depth_dev[k] for k in range(n)], seq.intr, seq.poses[:n],
+                                os.environ.get("TSDF_AUTOTUNE_CACHE"))
+        return tuned
+    return vol.launch_config()
+
+
 def raycast_algorithmic_bytes(counts, n_blocks, H, W, own_cull=True):
     """Unique bytes one raycast must move: the distinct 32-byte sectors of T
     and of the block table its samples read, the block list read by the range
@@ -340,16 +357,7 @@ def run_ours(args):
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume)
-    tuned = None
-    if args.launch_shape:
-        vpt, ctas, persistent = (int(x) for x in args.launch_shape.split(","))
-        vol.set_launch_config(integrate_voxels_per_thread=vpt, integrate_ctas_per_sm=ctas,
-                              raycast_persistent=persistent)
-    elif not args.no_autotune:
-        # launch shapes picked on the first frames (results do not depend on them)
-        n_tune = min(20, F)
-        tuned, _ = vol.autotune([depth_dev[k] for k in range(n_tune)], seq.intr, seq.poses[:n_tune],
-                                os.environ.get("TSDF_AUTOTUNE_CACHE"))
+    tuned = choose_launch(vol, args, depth_dev, seq)
     pipe = FusionPipeline(vol, seq.intr, dev, graph=args.mode == "graph")
     stream = torch.cuda.current_stream()
 
@@ -556,7 +564,7 @@ def run_extras(args):
     try:
         b = run_batched(sub_args(frames=1000), emit=False)
         out["batched_k8"] = keep(b, ["value", "unit", "ms_per_step", "config", "voxel_updates_per_s", "rays_per_s",
-                                     "work_per_step", "roofline_integrate_batch", "clocks"])
+                                     "work_per_step", "roofline_integrate_batch", "launch", "clocks"])
     except Exception as e:          # the room line stands on its own
         out["batched_k8"] = {"error": repr(e)}
     caps = {}
@@ -565,7 +573,7 @@ def run_extras(args):
             c = run_capsules(sub_args(frames=200, workload="capsules", storage=storage, oracle_sample=999),
                              emit=False)
             caps[storage] = keep(c, ["value", "unit", "ms_per_step", "voxel_updates_per_s", "rays_per_s", "dtype",
-                                     "pool_bytes_per_voxel", "error_vs_fp64_oracle", "clocks"])
+                                     "pool_bytes_per_voxel", "error_vs_fp64_oracle", "launch", "clocks"])
         except Exception as e:
             caps[storage] = {"error": repr(e)}
     out["capsules"] = {"config": "capsules: 1280x1024, 4096^3 grid of 0.15 mm voxels, 200 frames, one graph per "
@@ -603,6 +611,7 @@ def run_batched(args, emit=True):
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume)
+    shape = choose_launch(vol, args, depth_dev, seq)
     g = tsdf.Graph(vol, seq.intr, K)
     maps = (torch.empty((H, W), device=dev), torch.empty((H, W, 3), device=dev), torch.empty((H, W, 3), device=dev))
 
@@ -664,7 +673,7 @@ def run_batched(args, emit=True):
                                          "peak_kind": peak_kind, "traffic": None,
                                          "algorithmic_bytes_per_launch": integ_bytes / launches,
                                          "avg_launch_ms": integ_ms / launches},
-            "graph_instantiations": g.instantiations, "clocks": clk}
+            "launch": {"shape": shape}, "graph_instantiations": g.instantiations, "clocks": clk}
     g.close()
     vol.close()
     if emit:
@@ -727,6 +736,7 @@ def run_capsules(args, emit=True):
     F, H, W = seq.depth.shape
     depth_dev = torch.from_numpy(seq.depth).to(dev)
     vol = tsdf.Volume.from_params(seq.volume, storage=storage)
+    shape = choose_launch(vol, args, depth_dev, seq)
     pipe = FusionPipeline(vol, seq.intr, dev, graph=True)
 
     def step():
@@ -758,7 +768,7 @@ def run_capsules(args, emit=True):
             "rays_per_s": F * H * W * args.steps / sec,
             "work_per_step": {"voxel_updates": int(st["voxel_updates_total"]), "blocks": int(st["n_blocks"])},
             "pool_bytes_per_voxel": 4 + (4 if storage == tsdf.STORAGE_F32 else 2),
-            "algorithmic_bytes_per_update": bytes_per_update, "clocks": clk}
+            "algorithmic_bytes_per_update": bytes_per_update, "launch": {"shape": shape}, "clocks": clk}
     if args.oracle_sample > 0:
         ocoords, local, T, amb = capsule_oracle_reference(seq, args.oracle_sample)
         ge = vol.export()
