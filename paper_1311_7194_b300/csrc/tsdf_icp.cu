@@ -384,10 +384,28 @@ cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intri
     f.cos_min = prm.normal_cos_min;
     f.depth_min = v->cfg.depth_min;
     f.depth_max = v->cfg.depth_max;
-    const int grid = v->num_sms * 4;
+    // one wave: exactly the CTAs that can be resident at once (the kernel's
+    // registers fit 3 CTAs of 256 threads on an SM; a grid of 4 per SM ran
+    // its last quarter as a second wave)
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_reduce_kernel, kIcpThreads, 0) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    const int grid = v->num_sms * per_sm;
     if (!v->icp_part) {
         cudaError_t e = cudaMalloc(&v->icp_part, (size_t)grid * (kSums + 3) * sizeof(double) + 64 * sizeof(double));
         if (e != cudaSuccess) return e;
+    }
+    // the sums and the box lie next to each other on the device (kSums doubles,
+    // one spare, then 6 floats): one copy into pinned memory reads both
+    constexpr size_t kOutWords = kSums + 4;
+    if (!v->icp_host) {
+        cudaError_t e = cudaMallocHost(&v->icp_host, kOutWords * sizeof(double));
+        if (e != cudaSuccess) {
+            v->icp_host = nullptr;
+            return e;
+        }
     }
     double* part = v->icp_part;
     float* pbox = reinterpret_cast<float*>(part + (size_t)grid * kSums);          // grid * 6 floats
@@ -395,9 +413,12 @@ cudaError_t launch_icp_sums(tsdf_volume* v, const float* depth, const tsdf_intri
     float* box = reinterpret_cast<float*>(out + kSums + 1);                       // 6 floats
     icp_reduce_kernel<<<grid, kIcpThreads, 0, st>>>(f, depth, mv, mn, part, pbox);
     icp_final_kernel<<<kSums + 1, kIcpThreads, 0, st>>>(part, pbox, grid, out, box);
-    cudaError_t e = cudaMemcpyAsync(host_sums, out, kSums * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_box, box, 6 * sizeof(float), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(v->icp_host, out, kOutWords * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        std::memcpy(host_sums, v->icp_host, kSums * sizeof(double));
+        std::memcpy(host_box, v->icp_host + kSums + 1, 6 * sizeof(float));
+    }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -167,6 +167,7 @@ struct tsdf_volume {
     float2* meas_batch;            // [kMaxBatch * var_batch_stride] measurement maps of a batch
     int64_t var_batch_stride;
     double* icp_part;              // registration partial sums (lazily allocated)
+    double* icp_host;              // pinned host copy of one pass's sums and box (lazily allocated)
     void* mesh_scratch;            // marching cubes: per-block counts and offsets (lazily allocated)
     int mesh_table_ready;          // the case table is in constant memory
     int64_t frame;                 // host copy of the frame counter

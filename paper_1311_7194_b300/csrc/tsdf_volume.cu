@@ -97,6 +97,7 @@ void free_all(tsdf_volume* v) {
     cudaFree(v->meas);
     cudaFree(v->meas_batch);
     cudaFree(v->icp_part);
+    cudaFreeHost(v->icp_host);
     cudaFree(v->mesh_scratch);
 }
 
