@@ -254,12 +254,12 @@ def _sha(path):
 # when that source changes.
 NCU_TRAFFIC = {
     # frames 100-109, 10 launches each of depth_tiles + cull (which also makes
-    # the raycast's visible list) + integrate: 2144.8 MB over 76.55 M voxel updates
-    "integrate": {"sha": "9d7d503f6ec87abf", "bytes_per_unit": 28.02},
+    # the raycast's visible list) + integrate: 2185.9 MB over 76.55 M voxel updates
+    "integrate": {"sha": "808bf10e89c3e5aa", "bytes_per_unit": 28.56},
     # same frames, 10 launches each of raster + ray order + persistent raycast:
-    # 1014.7 MB against 783.8 MB of traced unique bytes, i.e. DRAM bytes per
+    # 1015.7 MB against 783.8 MB of traced unique bytes, i.e. DRAM bytes per
     # algorithmic byte
-    "raycast": {"sha": "e3bf95a41e672e86", "bytes_per_unit": 1.2946},
+    "raycast": {"sha": "e3bf95a41e672e86", "bytes_per_unit": 1.2959},
 }
 STAGE_SOURCES = {"integrate": "tsdf_integrate.cu", "raycast": "tsdf_raycast.cu"}
 TRACE_EVERY = 10

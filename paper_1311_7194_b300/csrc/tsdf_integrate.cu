@@ -473,6 +473,20 @@ __device__ __forceinline__ void update(const FrameParams& p, float& T, float& P,
     if (fabsf(T) > p.delta) T = __int_as_float(0x7fc00000);
 }
 
+// First voxel (x + 8 y + 64 z) of thread t's run of kVPT voxels along x. The
+// threads of a warp cover a box 4 voxels high in y (8 x 4 x 4 for 4 voxels a
+// thread, 8 x 4 x 8 for 8), so the measurement-map loads of one instruction
+// fall on about 4 image rows rather than 8.
+template <int kVPT>
+__device__ __forceinline__ int row_start(int t) {
+    if (kVPT == 4) {
+        const int xg = t & 1, y = ((t >> 1) & 3) | (((t >> 5) & 1) << 2), z = ((t >> 3) & 3) | (((t >> 6) & 1) << 2);
+        return 4 * xg + 8 * y + 64 * z;
+    }
+    const int y = (t & 3) | (((t >> 5) & 1) << 2), z = (t >> 2) & 7;
+    return 8 * y + 64 * z;
+}
+
 template <int kS, int kVPT, int kRule, bool kRefine>
 __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Counters* __restrict__ ctr,
                                                                         const VisibleBlock* __restrict__ vis,
@@ -483,7 +497,7 @@ __global__ void __launch_bounds__(kBlockVoxels / kVPT, 16) integrate_kernel(Coun
     pdl_prologue();
     static_assert(kVPT == 4 || kVPT == 8, "a thread owns 4 or 8 consecutive voxels of an x row");
     const unsigned nvis = ctr->n_visible;
-    const int v0 = threadIdx.x * kVPT;                    // first of this thread's voxels
+    const int v0 = row_start<kVPT>(threadIdx.x);          // first of this thread's voxels
     const float lx0 = (float)(v0 & 7), ly = (float)((v0 >> 3) & 7), lz = (float)(v0 >> 6);
     unsigned updates = 0;
     for (unsigned i = blockIdx.x; i < nvis; i += gridDim.x) {
