@@ -350,9 +350,13 @@ void tsdf_icp_params_default(tsdf_icp_params* p);
  * depth: device W*H floats of the frame; model_vertex / model_normal: device
  * W*H*3 floats (world, NaN = no surface) as written by tsdf_raycast with the
  * same intrinsics K at model_pose_wc. Synchronises with the stream once per
- * iteration (the pose lives on the host). *out (optional) receives the last
+ * iteration (the pose lives on the host); each iteration's sums and box reach
+ * the host in one copy through a small pinned buffer that the volume
+ * allocates on its first registration call (with the device buffer of the
+ * partial sums) and frees in tsdf_destroy. *out (optional) receives the last
  * iteration's statistics. An iteration with fewer than 6 pairs leaves the pose
- * unchanged. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA. */
+ * unchanged. Errors: TSDF_ERR_INVALID_ARG, TSDF_ERR_CUDA (also when either
+ * buffer cannot be allocated). */
 tsdf_status tsdf_icp(tsdf_volume* vol, const float* depth, const tsdf_intrinsics* K, const float* model_vertex,
                      const float* model_normal, const double model_pose_wc[16], const tsdf_icp_params* prm,
                      double pose_wc[16], tsdf_icp_result* out, void* stream);
