@@ -136,15 +136,15 @@ __device__ __forceinline__ void reset_frame_counters(Counters* ctr, bool rc_too)
 // is not a positive finite variance. One warp per tile, two pixels per lane.
 // Thread 0 also resets the call's counters when `reset` is given.
 template <bool kLearned>
-__global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth,
+__global__ void __launch_bounds__(256, 2) depth_tiles_kernel(const float* __restrict__ depth,
                                                           const float* __restrict__ var, FrameParams p,
                                                           float2* __restrict__ tiles, float2* __restrict__ meas,
                                                           Counters* __restrict__ reset, int reset_rc,
                                                           const __nv_bfloat16* __restrict__ mlp_w) {
     pdl_prologue();
-    __shared__ float smem[kLearned ? kSmemFloats : 1];
-    MlpShared mlp;
-    if (kLearned) mlp = load_weights(mlp_w, smem);
+    __shared__ __align__(16) float smem[kLearned ? kInferFloats : 4];
+    MlpInfer mlp;
+    if (kLearned) mlp = load_infer(mlp_w, smem);
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset, reset_rc != 0);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
     const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restric
         const int v = (t / tiles_x) * kDepthTile + (lane >> 2);
         float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
         if (v < p.height) {
-#pragma unroll
+            // the network's per-pixel state is large: one pixel at a time then
+#pragma unroll(kLearned ? 1 : 2)
             for (int k = 0; k < 2; ++k) {
                 if (u + k < p.width) {
                     const size_t pix = (size_t)v * p.width + u + k;

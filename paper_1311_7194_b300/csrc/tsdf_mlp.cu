@@ -43,8 +43,8 @@ constexpr float kHarvestBand = 4.0f;   // residuals kept: |r| <= kHarvestBand * 
 __global__ void __launch_bounds__(128) variance_mlp_kernel(const float* __restrict__ depth, FrameParams p,
                                                            const __nv_bfloat16* __restrict__ w,
                                                            float* __restrict__ var) {
-    __shared__ float smem[kSmemFloats];
-    const MlpShared m = load_weights(w, smem);
+    __shared__ __align__(16) float smem[kInferFloats];
+    const MlpInfer m = load_infer(w, smem);
     const int u = blockIdx.x * 16 + (threadIdx.x & 15);
     const int v = blockIdx.y * 8 + (threadIdx.x >> 4);
     if (u >= p.width || v >= p.height) return;
@@ -100,10 +100,11 @@ __global__ void __launch_bounds__(256) harvest_kernel(const float* __restrict__ 
 
 __global__ void __launch_bounds__(128) forward_kernel(const __nv_bfloat16* __restrict__ w, long long n,
                                                       const float* __restrict__ feats, float* __restrict__ out) {
-    __shared__ float smem[kSmemFloats];
-    const MlpShared m = load_weights(w, smem);
+    __shared__ __align__(16) float smem[kInferFloats];
+    const MlpInfer m = load_infer(w, smem);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         float f[kIn];
+#pragma unroll
         for (int i = 0; i < kIn; ++i) f[i] = feats[k * kIn + i];
         out[k] = mlp_eval(m, f);
     }

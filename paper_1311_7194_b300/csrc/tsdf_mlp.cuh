@@ -44,6 +44,42 @@ __device__ __forceinline__ MlpShared load_weights(const __nv_bfloat16* __restric
     return m;
 }
 
+// The inference layout: W1 and W2 transposed ([input][neuron], rows of 32
+// floats, 16-byte aligned), so one vector load from shared memory gives four
+// neurons' weights of the same input (a broadcast: every lane reads the same
+// address) and two paired multiply-adds consume them. kInferFloats floats.
+constexpr int kOffW2t = kHid * kIn + kHid, kOffB2t = kOffW2t + kHid * kHid;
+constexpr int kInferFloats = kOffB2t + 2 * kHid + 1;
+static_assert(kHid % 4 == 0 && (kHid * kIn) % 4 == 0 && kOffW2t % 4 == 0, "16-byte aligned rows");
+
+struct MlpInfer {
+    const float* W1t;   // [27][32]
+    const float* b1;
+    const float* W2t;   // [32][32]
+    const float* b2;
+    const float* W3;
+    float b3;
+};
+
+// smem: kInferFloats floats, 16-byte aligned.
+__device__ __forceinline__ MlpInfer load_infer(const __nv_bfloat16* __restrict__ w, float* smem) {
+    for (int e = threadIdx.x; e < kHid * kIn; e += blockDim.x)
+        smem[(e % kIn) * kHid + e / kIn] = __bfloat162float(w[e]);              // W1[j][i] -> W1t[i][j]
+    for (int j = threadIdx.x; j < kHid; j += blockDim.x) smem[kHid * kIn + j] = __bfloat162float(w[kOffB1 + j]);
+    for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x)
+        smem[kOffW2t + (e % kHid) * kHid + e / kHid] = __bfloat162float(w[kOffW2 + e]);   // W2[j][i] -> W2t[i][j]
+    for (int i = threadIdx.x; i < 2 * kHid + 1; i += blockDim.x) smem[kOffB2t + i] = __bfloat162float(w[kOffB2 + i]);
+    __syncthreads();
+    MlpInfer m;
+    m.W1t = smem;
+    m.b1 = smem + kHid * kIn;
+    m.W2t = smem + kOffW2t;
+    m.b2 = smem + kOffB2t;
+    m.W3 = smem + kOffB2t + kHid;
+    m.b3 = smem[kOffB2t + 2 * kHid];
+    return m;
+}
+
 // Features of pixel (u, v); false when its depth is not a valid measurement.
 __device__ __forceinline__ bool pixel_features(const float* __restrict__ depth, const FrameParams& p, int u, int v,
                                                float f[kIn]) {
@@ -80,22 +116,58 @@ __device__ __forceinline__ bool pixel_features(const float* __restrict__ depth, 
     return true;
 }
 
-__device__ __forceinline__ float mlp_eval(const MlpShared& m, const float f[kIn]) {
+// The network's output for features f. Each neuron's sum runs over its inputs
+// in order, one fused multiply-add each (two neurons per paired instruction,
+// which rounds both as the scalar one), and the output sums the neurons in
+// order: the same operations as a plain loop over the row-major weights.
+__device__ __forceinline__ float mlp_eval(const MlpInfer& m, const float f[kIn]) {
+    // the weights stay in shared memory: without this barrier the compiler
+    // treats their loads as invariant across the caller's pixel loop, hoists
+    // all of them and spills them to local memory
+    asm volatile("" ::: "memory");
+    float2 acc[kHid / 2];
+#pragma unroll
+    for (int j = 0; j < kHid / 2; ++j) acc[j] = make_float2(m.b1[2 * j], m.b1[2 * j + 1]);
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) {
+        const float2 x = make_float2(f[i], f[i]);
+        const float4* w = reinterpret_cast<const float4*>(m.W1t + i * kHid);
+#pragma unroll
+        for (int q = 0; q < kHid / 4; ++q) {
+            const float4 w4 = w[q];
+            acc[2 * q] = __ffma2_rn(make_float2(w4.x, w4.y), x, acc[2 * q]);
+            acc[2 * q + 1] = __ffma2_rn(make_float2(w4.z, w4.w), x, acc[2 * q + 1]);
+        }
+    }
     float a1[kHid];
 #pragma unroll
-    for (int j = 0; j < kHid; ++j) {
-        float acc = m.b1[j];
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) acc = fmaf(m.W1[j * kIn + i], f[i], acc);
-        a1[j] = fmaxf(acc, 0.0f);
+    for (int j = 0; j < kHid / 2; ++j) {
+        a1[2 * j] = fmaxf(acc[j].x, 0.0f);
+        a1[2 * j + 1] = fmaxf(acc[j].y, 0.0f);
     }
+    // the second layer in two halves of 16 neurons (registers)
     float out = m.b3;
 #pragma unroll
-    for (int j = 0; j < kHid; ++j) {
-        float acc = m.b2[j];
+    for (int h = 0; h < 2; ++h) {
+        float2 acc2[kHid / 4];
 #pragma unroll
-        for (int i = 0; i < kHid; ++i) acc = fmaf(m.W2[j * kW2Pitch + i], a1[i], acc);
-        out = fmaf(m.W3[j], fmaxf(acc, 0.0f), out);
+        for (int j = 0; j < kHid / 4; ++j) acc2[j] = make_float2(m.b2[h * kHid / 2 + 2 * j], m.b2[h * kHid / 2 + 2 * j + 1]);
+#pragma unroll
+        for (int i = 0; i < kHid; ++i) {
+            const float2 x = make_float2(a1[i], a1[i]);
+            const float4* w = reinterpret_cast<const float4*>(m.W2t + i * kHid + h * kHid / 2);
+#pragma unroll
+            for (int q = 0; q < kHid / 8; ++q) {
+                const float4 w4 = w[q];
+                acc2[2 * q] = __ffma2_rn(make_float2(w4.x, w4.y), x, acc2[2 * q]);
+                acc2[2 * q + 1] = __ffma2_rn(make_float2(w4.z, w4.w), x, acc2[2 * q + 1]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kHid / 4; ++j) {
+            out = fmaf(m.W3[h * kHid / 2 + 2 * j], fmaxf(acc2[j].x, 0.0f), out);
+            out = fmaf(m.W3[h * kHid / 2 + 2 * j + 1], fmaxf(acc2[j].y, 0.0f), out);
+        }
     }
     return out;
 }
@@ -105,7 +177,7 @@ __device__ __forceinline__ float mlp_eval(const MlpShared& m, const float f[kIn]
 // times noisier than the quadratic model says - a sensor far poorer at depth
 // edges - or 4 times less noisy); 0 (no measurement) when the pixel's depth is
 // not a valid measurement.
-__device__ __forceinline__ float learned_variance(const MlpShared& m, const float* __restrict__ depth,
+__device__ __forceinline__ float learned_variance(const MlpInfer& m, const float* __restrict__ depth,
                                                   const FrameParams& p, int u, int v) {
     float f[kIn];
     if (!pixel_features(depth, p, u, v, f)) return 0.0f;
