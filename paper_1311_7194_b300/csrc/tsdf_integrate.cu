@@ -130,21 +130,15 @@ __device__ __forceinline__ void reset_frame_counters(Counters* ctr, bool rc_too)
 
 // Per 8x8-pixel tile: (min, max) of the valid measured depth, (+inf, -inf) when
 // the tile has none. Per pixel: meas = (D, p_k), p_k from the variance map when
-// one is given, from the learned-variance network when kLearned (evaluated here,
-// per pixel, with its weights staged in shared memory once per CTA), else the
-// quadratic model (a D^2)^2; D becomes NaN when it is not a valid depth or p_k
-// is not a positive finite variance. One warp per tile, two pixels per lane.
-// Thread 0 also resets the call's counters when `reset` is given.
-template <bool kLearned>
-__global__ void __launch_bounds__(256, 2) depth_tiles_kernel(const float* __restrict__ depth,
+// one is given, else the quadratic model (a D^2)^2; D becomes NaN when it is
+// not a valid depth or p_k is not a positive finite variance. One warp per
+// tile, two pixels per lane. Thread 0 also resets the call's counters when
+// `reset` is given.
+__global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restrict__ depth,
                                                           const float* __restrict__ var, FrameParams p,
                                                           float2* __restrict__ tiles, float2* __restrict__ meas,
-                                                          Counters* __restrict__ reset, int reset_rc,
-                                                          const __nv_bfloat16* __restrict__ mlp_w) {
+                                                          Counters* __restrict__ reset, int reset_rc) {
     pdl_prologue();
-    __shared__ __align__(16) float smem[kLearned ? kInferFloats : 4];
-    MlpInfer mlp;
-    if (kLearned) mlp = load_infer(mlp_w, smem);
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset, reset_rc != 0);
     const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
     const int tiles_y = (p.height + kDepthTile - 1) / kDepthTile;
@@ -155,8 +149,7 @@ __global__ void __launch_bounds__(256, 2) depth_tiles_kernel(const float* __rest
         const int v = (t / tiles_x) * kDepthTile + (lane >> 2);
         float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
         if (v < p.height) {
-            // the network's per-pixel state is large: one pixel at a time then
-#pragma unroll(kLearned ? 1 : 2)
+#pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (u + k < p.width) {
                     const size_t pix = (size_t)v * p.width + u + k;
@@ -167,9 +160,7 @@ __global__ void __launch_bounds__(256, 2) depth_tiles_kernel(const float* __rest
                         hi = fmaxf(hi, d);
                     }
                     float pv;
-                    if (kLearned) {
-                        pv = learned_variance(mlp, depth, p, u + k, v);
-                    } else if (var) {
+                    if (var) {
                         pv = __ldg(var + pix);
                     } else {
                         const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
@@ -186,6 +177,150 @@ __global__ void __launch_bounds__(256, 2) depth_tiles_kernel(const float* __rest
             hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
         if (lane == 0) tiles[t] = make_float2(lo, hi);
+    }
+}
+
+// depth_tiles with the learned-variance network giving each pixel's p_k. A
+// CTA of kMlpThreads threads takes kMlpTiles 8x8 tiles per pass, one pixel per
+// thread: it stages the pixels' features in shared memory (transposed, input
+// by pixel), evaluates both layers for all its pixels as register tiles of 4
+// pixels x 8 neurons per thread (a warp shares one group of 8 neurons, so each
+// weight is a broadcast load that serves 4 pixels, and each feature load serves
+// 8 neurons), and sums each pixel's output over the neurons in order. Every
+// neuron's sum runs over its inputs in order, one fused multiply-add each, so
+// the outputs are those of mlp_eval bit for bit.
+constexpr int kMlpThreads = 128;
+constexpr int kMlpTiles = kMlpThreads / (kDepthTile * kDepthTile);   // 2
+static_assert(kMlpThreads == 4 * 32 && kHid == 32, "4 pixel groups of 32 threads, 4 neuron groups of 8");
+
+__global__ void __launch_bounds__(kMlpThreads) depth_tiles_mlp_kernel(const float* __restrict__ depth, FrameParams p,
+                                                                      float2* __restrict__ tiles,
+                                                                      float2* __restrict__ meas,
+                                                                      Counters* __restrict__ reset, int reset_rc,
+                                                                      const __nv_bfloat16* __restrict__ mlp_w) {
+    pdl_prologue();
+    __shared__ __align__(16) float smem[kInferFloats];
+    __shared__ __align__(16) float sA[kHid][kMlpThreads];   // features [input][pixel], then layer-2 outputs
+    __shared__ __align__(16) float sH[kHid][kMlpThreads];   // layer-1 outputs [neuron][pixel]
+    __shared__ float2 sTile[kMlpThreads / 32];
+    const MlpInfer m = load_infer(mlp_w, smem);
+    if (reset && blockIdx.x == 0 && threadIdx.x == 0) reset_frame_counters(reset, reset_rc != 0);
+    const int tiles_x = (p.width + kDepthTile - 1) / kDepthTile;
+    const int n_tiles = tiles_x * ((p.height + kDepthTile - 1) / kDepthTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = threadIdx.x;                        // this thread's pixel in the pass
+    const int pg = lane, ng = warp;                    // register tile: pixels 4 pg.., neurons 8 ng..
+    for (int base = blockIdx.x * kMlpTiles; base < n_tiles; base += gridDim.x * kMlpTiles) {
+        // the pixel: tile base + px / 64, row (px / 8) % 8, column px % 8
+        const int t = base + px / (kDepthTile * kDepthTile);
+        const int q = px % (kDepthTile * kDepthTile);
+        const int u = (t % tiles_x) * kDepthTile + q % kDepthTile;
+        const int v = (t / tiles_x) * kDepthTile + q / kDepthTile;
+        const bool in = t < n_tiles && u < p.width && v < p.height;
+        float d = 0.0f, pq = 0.0f;
+        bool valid = false, fok = false;
+        float f[kIn];
+        if (in) {
+            d = __ldg(depth + (size_t)v * p.width + u);
+            valid = depth_ok(d, p.depth_min, p.depth_max);
+            const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
+            pq = __fmul_rn(sg, sg);
+            fok = pixel_features(depth, p, u, v, f);
+        }
+#pragma unroll
+        for (int i = 0; i < kIn; ++i) sA[i][px] = fok ? f[i] : 0.0f;
+        // tile depth range: each warp holds half a tile
+        float lo = valid ? d : __int_as_float(0x7f800000), hi = valid ? d : -__int_as_float(0x7f800000);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) sTile[warp] = make_float2(lo, hi);
+        __syncthreads();
+        if (threadIdx.x < kMlpTiles && base + threadIdx.x < n_tiles) {
+            const float2 a = sTile[2 * threadIdx.x], b = sTile[2 * threadIdx.x + 1];
+            tiles[base + threadIdx.x] = make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
+        }
+        // layer 1: sH[j][pixel] = relu(b1[j] + sum_i W1[j][i] f[pixel][i])
+        {
+            float2 acc[4][4];   // [pixel][neuron pair]
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(m.b1[8 * ng + 2 * c], m.b1[8 * ng + 2 * c + 1]);
+            asm volatile("" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) {
+                const float4 x = *reinterpret_cast<const float4*>(&sA[i][4 * pg]);
+                const float4 w0 = *reinterpret_cast<const float4*>(m.W1t + i * kHid + 8 * ng);
+                const float4 w1 = *reinterpret_cast<const float4*>(m.W1t + i * kHid + 8 * ng + 4);
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 xr = make_float2(xs[r], xs[r]);
+                    acc[r][0] = __ffma2_rn(make_float2(w0.x, w0.y), xr, acc[r][0]);
+                    acc[r][1] = __ffma2_rn(make_float2(w0.z, w0.w), xr, acc[r][1]);
+                    acc[r][2] = __ffma2_rn(make_float2(w1.x, w1.y), xr, acc[r][2]);
+                    acc[r][3] = __ffma2_rn(make_float2(w1.z, w1.w), xr, acc[r][3]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                *reinterpret_cast<float4*>(&sH[8 * ng + 2 * c][4 * pg]) =
+                    make_float4(fmaxf(acc[0][c].x, 0.0f), fmaxf(acc[1][c].x, 0.0f), fmaxf(acc[2][c].x, 0.0f),
+                                fmaxf(acc[3][c].x, 0.0f));
+                *reinterpret_cast<float4*>(&sH[8 * ng + 2 * c + 1][4 * pg]) =
+                    make_float4(fmaxf(acc[0][c].y, 0.0f), fmaxf(acc[1][c].y, 0.0f), fmaxf(acc[2][c].y, 0.0f),
+                                fmaxf(acc[3][c].y, 0.0f));
+            }
+        }
+        __syncthreads();
+        // layer 2: sA[j][pixel] = relu(b2[j] + sum_i W2[j][i] sH[i][pixel])
+        {
+            float2 acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(m.b2[8 * ng + 2 * c], m.b2[8 * ng + 2 * c + 1]);
+            asm volatile("" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < kHid; ++i) {
+                const float4 x = *reinterpret_cast<const float4*>(&sH[i][4 * pg]);
+                const float4 w0 = *reinterpret_cast<const float4*>(m.W2t + i * kHid + 8 * ng);
+                const float4 w1 = *reinterpret_cast<const float4*>(m.W2t + i * kHid + 8 * ng + 4);
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 xr = make_float2(xs[r], xs[r]);
+                    acc[r][0] = __ffma2_rn(make_float2(w0.x, w0.y), xr, acc[r][0]);
+                    acc[r][1] = __ffma2_rn(make_float2(w0.z, w0.w), xr, acc[r][1]);
+                    acc[r][2] = __ffma2_rn(make_float2(w1.x, w1.y), xr, acc[r][2]);
+                    acc[r][3] = __ffma2_rn(make_float2(w1.z, w1.w), xr, acc[r][3]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                *reinterpret_cast<float4*>(&sA[8 * ng + 2 * c][4 * pg]) =
+                    make_float4(fmaxf(acc[0][c].x, 0.0f), fmaxf(acc[1][c].x, 0.0f), fmaxf(acc[2][c].x, 0.0f),
+                                fmaxf(acc[3][c].x, 0.0f));
+                *reinterpret_cast<float4*>(&sA[8 * ng + 2 * c + 1][4 * pg]) =
+                    make_float4(fmaxf(acc[0][c].y, 0.0f), fmaxf(acc[1][c].y, 0.0f), fmaxf(acc[2][c].y, 0.0f),
+                                fmaxf(acc[3][c].y, 0.0f));
+            }
+        }
+        __syncthreads();
+        if (in) {
+            float out = m.b3;
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) out = fmaf(m.W3[j], sA[j][px], out);
+            // learned_variance's decision: 0 without features, p_quad outside [-ln 4, ln 64]
+            const float pv = !fok ? 0.0f
+                             : (out >= -1.3862943611198906f && out <= 4.1588830833596715f) ? pq * expf(out) : pq;
+            const bool use = valid && pv > 0.0f && pv <= 3.0e38f;
+            meas[(size_t)v * p.width + u] = make_float2(use ? d : __int_as_float(0x7fc00000), pv);
+        }
+        __syncthreads();   // sA and sTile are rewritten by the next pass
     }
 }
 
@@ -690,11 +825,11 @@ void launch_depth_tiles(tsdf_volume* v, const float* depth, const float* var, co
                         float2* meas, Counters* reset, bool reset_rc, cudaStream_t st) {
     const auto* w = static_cast<const __nv_bfloat16*>(v->mlp_w);
     if (!var && w)
-        launch_pdl(depth_tiles_kernel<true>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
+        launch_pdl(depth_tiles_mlp_kernel, dim3(v->num_sms * 8), dim3(kMlpThreads), st, depth, p, tiles, meas, reset,
                    (int)reset_rc, w);
     else
-        launch_pdl(depth_tiles_kernel<false>, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
-                   (int)reset_rc, w);
+        launch_pdl(depth_tiles_kernel, dim3(v->num_sms * 4), dim3(256), st, depth, var, p, tiles, meas, reset,
+                   (int)reset_rc);
 }
 
 cudaError_t launch_integrate(tsdf_volume* v, const float* depth, const float* var, const FrameParams& p,
