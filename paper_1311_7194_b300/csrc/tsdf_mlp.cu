@@ -8,13 +8,14 @@
 // its 5x5 depth patch (differences to the centre over delta, clamped to
 // [-1, 1], +1 where a neighbour is missing), depth / 4 and the incidence cosine
 // from the depth map's central differences; p_k = p_quad exp(out), falling back
-// to p_quad when |out| > ln 4 or out is not finite. Parameters: W1[32][27],
+// to p_quad when out lies outside [-ln 4, ln 64] or is not finite. Parameters: W1[32][27],
 // b1[32], W2[32][32], b2[32], W3[32], b3.
 //
 //   inference (tsdf_mlp.cuh): weights decoded once per CTA into shared memory
-//       (read as broadcasts). The integrate stage evaluates the network per
-//       pixel inside depth_tiles, where it forms the measurement map (D, p_k)
-//       (tsdf_integrate with a network set and no variance map);
+//       (read as broadcasts). The integrate stage evaluates the network inside
+//       depth_tiles_mlp_kernel, where it forms the measurement map (D, p_k)
+//       (tsdf_integrate with a network set and no variance map), as register
+//       tiles of pixels x neurons with the same operations as mlp_eval;
 //       variance_mlp_kernel writes the same p_k as a map (tsdf_mlp_variance).
 //   harvest_kernel: training pairs from a measured depth map and the model's
 //       raycast at the same pose: features and s = r^2 / p_quad for pixels whose

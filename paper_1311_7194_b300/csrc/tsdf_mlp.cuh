@@ -2,7 +2,8 @@
 // perceptron with ReLU and bfloat16 weights; see tsdf_mlp.cu): weight staging
 // in shared memory, the per-pixel features, the forward pass and the variance
 // it gives. Shared by the network's own kernels and by the integrate stage,
-// which evaluates it where it forms each pixel's measurement (depth_tiles).
+// which evaluates it where it forms each pixel's measurement
+// (depth_tiles_mlp_kernel, with the same operations as mlp_eval).
 #pragma once
 
 #include <cuda_bf16.h>
