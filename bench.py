@@ -254,8 +254,8 @@ def _sha(path):
 # when that source changes.
 NCU_TRAFFIC = {
     # frames 100-109, 10 launches each of depth_tiles + cull (which also makes
-    # the raycast's visible list) + integrate: 2185.9 MB over 76.55 M voxel updates
-    "integrate": {"sha": "808bf10e89c3e5aa", "bytes_per_unit": 28.56},
+    # the raycast's visible list) + integrate: 2185.1 MB over 76.55 M voxel updates
+    "integrate": {"sha": "970d6d56551aa5a6", "bytes_per_unit": 28.55},
     # same frames, 10 launches each of raster + ray order + persistent raycast:
     # 1015.7 MB against 783.8 MB of traced unique bytes, i.e. DRAM bytes per
     # algorithmic byte
