@@ -153,6 +153,46 @@ def test_variance_map_and_fusion_match_oracle():
     assert v["ok"], json.dumps(v)
 
 
+def _same_volume(a, b):
+    ea, eb = a.export(), b.export()
+    assert np.array_equal(ea.coords, eb.coords) and np.array_equal(ea.alloc_frame, eb.alloc_frame)
+    chi = np.isnan(ea.T)
+    assert np.array_equal(chi, np.isnan(eb.T))
+    assert np.array_equal(ea.T[~chi], eb.T[~chi]) and np.array_equal(ea.P[~chi], eb.P[~chi])
+    return int((~chi).sum())
+
+
+def test_network_in_the_integrate_stage_equals_its_map_and_batches():
+    """The integrate stage evaluates the network as register tiles of pixels x
+    neurons (depth_tiles_mlp_kernel); fusing with it must equal, bit for bit,
+    fusing with the per-pixel evaluation's variance map (tsdf_mlp_variance), on
+    a ragged image whose edge tiles are partly outside it. K-batched fusion with
+    the network set must equal the sequential fusion bit for bit."""
+    seq = synth.room_sequence(n_frames=8, width=157, height=117, grid_dim=512, voxel_size=6e-3,
+                              block_capacity=1 << 16)
+    bits = _random_bits(7, scale_out=0.5)
+    wq = torch.from_numpy(bits.view(np.int16)).cuda()
+    K = tsdf.intrinsics(seq.intr)
+    tiled, mapped, batched = (tsdf.Volume.from_params(seq.volume) for _ in range(3))
+    tiled.set_variance_mlp(bits)
+    batched.set_variance_mlp(bits)
+    d = [torch.from_numpy(x).cuda() for x in seq.depth]
+    for k in range(seq.n_frames):
+        tiled.fuse(d[k], seq.intr, seq.poses[k])
+        var = torch.empty_like(d[k])
+        assert mapped.lib.tsdf_mlp_variance(mapped.h, _p(wq), _p(d[k]), ctypes.byref(K), _p(var), None) == tsdf.OK
+        mapped.fuse(d[k], seq.intr, seq.poses[k], variance=var)
+    for k in range(0, seq.n_frames, 4):
+        batched.integrate_batch(d[k:k + 4], seq.intr, seq.poses[k:k + 4])
+    torch.cuda.synchronize()
+    for v in (tiled, mapped, batched):
+        v.check()
+    assert _same_volume(tiled, mapped) > 10000
+    assert _same_volume(tiled, batched) > 10000
+    for v in (tiled, mapped, batched):
+        v.close()
+
+
 def _scenes(seeds, n_frames, **kw):
     return [synth.room_sequence(seed=sd, n_frames=n_frames, width=320, height=240, grid_dim=1024, voxel_size=3e-3,
                                 block_capacity=1 << 18, device="cuda", **kw) for sd in seeds]
