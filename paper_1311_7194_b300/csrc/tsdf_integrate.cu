@@ -188,10 +188,16 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float* __restric
 // weight is a broadcast load that serves 4 pixels, and each feature load serves
 // 8 neurons), and sums each pixel's output over the neurons in order. Every
 // neuron's sum runs over its inputs in order, one fused multiply-add each, so
-// the outputs are those of mlp_eval bit for bit.
+// the outputs are those of mlp_eval bit for bit. The features read a 5x5
+// window around each pixel: each pass first copies its tiles' depths with a
+// 2-pixel halo (12x12 per tile, NaN outside the image, which no validity test
+// accepts, as none accepts a pixel outside it) into shared memory, rows
+// kPatchPitch floats apart so that a warp's 4x8 pixels fall on 32 banks.
 constexpr int kMlpThreads = 128;
 constexpr int kMlpTiles = kMlpThreads / (kDepthTile * kDepthTile);   // 2
 static_assert(kMlpThreads == 4 * 32 && kHid == 32, "4 pixel groups of 32 threads, 4 neuron groups of 8");
+constexpr int kHalo = 2, kPatch = kDepthTile + 2 * kHalo, kPatchPitch = 24, kPatchFloats = kPatch * kPatchPitch;
+static_assert(kPatch <= kPatchPitch && kMlpTiles * kPatchFloats <= kHid * kMlpThreads, "the patches fit in sH");
 
 __global__ void __launch_bounds__(kMlpThreads) depth_tiles_mlp_kernel(const float* __restrict__ depth, FrameParams p,
                                                                       float2* __restrict__ tiles,
@@ -217,15 +223,33 @@ __global__ void __launch_bounds__(kMlpThreads) depth_tiles_mlp_kernel(const floa
         const int u = (t % tiles_x) * kDepthTile + q % kDepthTile;
         const int v = (t / tiles_x) * kDepthTile + q / kDepthTile;
         const bool in = t < n_tiles && u < p.width && v < p.height;
+        // the depth patches (sH is free here: the previous pass read it before its last two barriers)
+        float* patch = &sH[0][0];
+        for (int e = threadIdx.x; e < kMlpTiles * kPatch * kPatch; e += kMlpThreads) {
+            const int i = e / (kPatch * kPatch), r = (e / kPatch) % kPatch, c = e % kPatch;
+            const int ti = base + i;
+            const int x = (ti % tiles_x) * kDepthTile - kHalo + c, y = (ti / tiles_x) * kDepthTile - kHalo + r;
+            float dv = __int_as_float(0x7fc00000);
+            if (ti < n_tiles && x >= 0 && y >= 0 && x < p.width && y < p.height)
+                dv = __ldg(depth + (size_t)y * p.width + x);
+            patch[i * kPatchFloats + r * kPatchPitch + c] = dv;
+        }
+        __syncthreads();
+        // this pixel's patch and the image coordinates of its first entry
+        const float* pt = patch + (px / (kDepthTile * kDepthTile)) * kPatchFloats;
+        const int ox = u - q % kDepthTile - kHalo, oy = v - q / kDepthTile - kHalo;
+        auto D = [&](int x, int y, float* dd) {
+            *dd = pt[(y - oy) * kPatchPitch + (x - ox)];
+            return depth_ok(*dd, p.depth_min, p.depth_max);
+        };
         float d = 0.0f, pq = 0.0f;
         bool valid = false, fok = false;
         float f[kIn];
         if (in) {
-            d = __ldg(depth + (size_t)v * p.width + u);
-            valid = depth_ok(d, p.depth_min, p.depth_max);
+            valid = D(u, v, &d);
             const float sg = __fmul_rn(__fmul_rn(p.sigma_coeff, d), d);
             pq = __fmul_rn(sg, sg);
-            fok = pixel_features(depth, p, u, v, f);
+            fok = features_from(D, p, u, v, f);
         }
 #pragma unroll
         for (int i = 0; i < kIn; ++i) sA[i][px] = fok ? f[i] : 0.0f;
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kMlpThreads) depth_tiles_mlp_kernel(const floa
             const bool use = valid && pv > 0.0f && pv <= 3.0e38f;
             meas[(size_t)v * p.width + u] = make_float2(use ? d : __int_as_float(0x7fc00000), pv);
         }
-        __syncthreads();   // sA and sTile are rewritten by the next pass
+        __syncthreads();   // sA, sTile and sH are rewritten by the next pass
     }
 }
 

@@ -82,13 +82,10 @@ __device__ __forceinline__ MlpInfer load_infer(const __nv_bfloat16* __restrict__
 }
 
 // Features of pixel (u, v); false when its depth is not a valid measurement.
-__device__ __forceinline__ bool pixel_features(const float* __restrict__ depth, const FrameParams& p, int u, int v,
-                                               float f[kIn]) {
-    auto D = [&](int x, int y, float* d) {
-        if (x < 0 || y < 0 || x >= p.width || y >= p.height) return false;
-        *d = __ldg(depth + (size_t)y * p.width + x);
-        return depth_ok(*d, p.depth_min, p.depth_max);
-    };
+// D(x, y, &d) reads the depth at pixel (x, y) into d and tells whether it is
+// a valid measurement (false outside the image).
+template <class DepthAt>
+__device__ __forceinline__ bool features_from(DepthAt D, const FrameParams& p, int u, int v, float f[kIn]) {
     float d0;
     if (!D(u, v, &d0)) return false;
     const float inv_delta = 1.0f / p.delta;
@@ -115,6 +112,16 @@ __device__ __forceinline__ bool pixel_features(const float* __restrict__ depth, 
         if (ln > 0.0f && lp > 0.0f) f[26] = fabsf(n0 * P0 + n1 * P1 + n2 * P2) / (ln * lp);
     }
     return true;
+}
+
+__device__ __forceinline__ bool pixel_features(const float* __restrict__ depth, const FrameParams& p, int u, int v,
+                                               float f[kIn]) {
+    auto D = [&](int x, int y, float* d) {
+        if (x < 0 || y < 0 || x >= p.width || y >= p.height) return false;
+        *d = __ldg(depth + (size_t)y * p.width + x);
+        return depth_ok(*d, p.depth_min, p.depth_max);
+    };
+    return features_from(D, p, u, v, f);
 }
 
 // The network's output for features f. Each neuron's sum runs over its inputs
